@@ -1,0 +1,434 @@
+"""Benchmark: Matlab-compatible sparse assembly on the 3D P1 tetrahedral cube.
+
+One step = one full assembly S = sparse(i,j,s,m,n) of the 100^3-vertex Kuhn
+cube (93,148,704 triplets, no plan reuse) followed by 50 numeric-only
+re-assemblies of the same pattern with fresh values (rotating 4 value
+buffers), as in a time-dependent nonlinear PDE solve.  The metric is
+G triplets/s over the whole job (51 assemblies of L triplets per step);
+the JSON line also reports the full and numeric-only phases separately,
+the HBM roofline of the dominant kernel (the numeric fold), the batched vs
+plain comparison on 256 uneven instances, an end-to-end figure through
+host buffers, clocks, and the CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank assembles its own
+replica (independent problems, no collective on the data path); the
+timing is the max over ranks and the value is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1406_1066_gb300 import inputs  # noqa: E402
+
+WORKLOAD = "mesh3d_100"
+NUMERIC_STEPS = 50
+VALUE_SEEDS = (1409, 1410, 1411, 1412)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_desc(t) -> str:
+    N = t.meta.get("N")
+    return (f"{t.name}: 3D P1 Kuhn-tetrahedral cube, {N}^3 vertices (m=n={t.m}), "
+            f"{(N - 1) ** 3 * 6} tets, L={t.L} int32 1-based triplets in element order, "
+            f"FP64 values U(-1,1); full assembly then {NUMERIC_STEPS} numeric re-assemblies")
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash(*files) -> str:
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1406_1066_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(summary: str, src_hash: str):
+    """DRAM bytes per launch from a committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha1") != src_hash:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.tmp.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+def oracle_job(t, frac_den: int, numeric_steps: int):
+    """Run the oracle on the first L/frac_den triplets (element order); return (seconds, L_s)."""
+    import oracle
+    Ls = (t.L // frac_den) // 16 * 16
+    ii, jj, s = t.ii[:Ls].copy(), t.jj[:Ls].copy(), t.s[:Ls].copy()
+    vals = [inputs.mesh_values(Ls, 9000 + k) for k in range(4)]
+    t0 = time.perf_counter()
+    r = oracle.assemble(ii, jj, s, t.m, t.n)
+    for k in range(numeric_steps):
+        oracle.numeric(r.irank, vals[k % 4], r.nnz)
+    return time.perf_counter() - t0, Ls
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    t = inputs.workload(WORKLOAD)
+    den = 16
+    for _ in range(args.warmup):
+        oracle_job(t, den, NUMERIC_STEPS)
+    times = []
+    Ls = 0
+    for _ in range(args.steps):
+        sec, Ls = oracle_job(t, den, NUMERIC_STEPS)
+        times.append(sec)
+    per = statistics.mean(times)
+    value = Ls * (1 + NUMERIC_STEPS) / per / 1e9
+    sample = (f"first {Ls} triplets (1/{den} of the cube in element order): one oracle assembly "
+              f"+ {NUMERIC_STEPS} oracle numeric passes per step, single thread")
+    line = {"impl": "reference", "metric": "G triplets/s (full assembly + 50 numeric re-assemblies)",
+            "value": value, "unit": "G triplets/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "G triplets/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "G triplets/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def batched_vs_plain(torch, fsparse, to_dev, steps: int = 100):
+    """256 uneven mesh instances: 100 graph-replayed batched steps vs per-plan launches."""
+    b = inputs.batch(256, 1416)
+    plans = [fsparse.symbolic(to_dev(t.ii), to_dev(t.jj), t.m, t.n) for t in b.instances]
+    bt = fsparse.Batch(plans)
+    total = bt.len_off[-1]
+    vals = [torch.from_numpy(inputs.mesh_values(total, 1416 + k)).to("cuda") for k in range(2)]
+    s_buf = torch.empty(total, dtype=torch.float64, device="cuda")
+    out_b = torch.empty(bt.nnz_off[-1], dtype=torch.float64, device="cuda")
+    outs_p = [torch.empty(p.cap, dtype=torch.float64, device="cuda") for p in plans]
+    views = [s_buf[bt.len_off[i]:bt.len_off[i + 1]] for i in range(len(plans))]
+
+    def plain_step():
+        for p, v, o in zip(plans, views, outs_p):
+            fsparse.numeric(p, v, o)
+
+    s_buf.copy_(vals[0])
+    bt.numeric(s_buf, out_b)
+    plain_step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bt.numeric(s_buf, out_b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = fsparse.fsparse_kernel_launches()
+    e0.record()
+    for k in range(steps):
+        s_buf.copy_(vals[k & 1])
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / steps
+    e0.record()
+    for k in range(steps):
+        s_buf.copy_(vals[k & 1])
+        plain_step()
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / steps
+    # identical results (last step used vals[(steps-1)&1] in both)
+    same = all(torch.equal(out_b[bt.nnz_off[i]:bt.nnz_off[i + 1]], outs_p[i][: plans[i].nnz])
+               for i in range(len(plans)))
+    res = {"instances": len(plans), "total_triplets": total, "steps": steps,
+           "batched_ms_per_step": batched_ms, "plain_ms_per_step": plain_ms,
+           "batched_gtps": total / batched_ms / 1e6, "plain_gtps": total / plain_ms / 1e6,
+           "speedup": plain_ms / batched_ms, "identical": bool(same),
+           "note": "each step includes a device copy of the step's values into the bound buffer"}
+    bt.close()
+    for p in plans:
+        p.close()
+    return res
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_1406_1066_gb300 import fsparse
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    t = inputs.workload(WORKLOAD)
+    L = t.L
+    ii_d, jj_d = to_dev(t.ii), to_dev(t.jj)
+    vals = [to_dev(t.s)] + [to_dev(inputs.mesh_values(L, sd)) for sd in VALUE_SEEDS[1:]]
+    prS = torch.empty(L, dtype=torch.float64, device=dev)
+    out = torch.empty(L, dtype=torch.float64, device=dev)
+    cfg = fsparse.fsparse_get_config(L, t.m, t.n)
+
+    def step(timing=None):
+        if timing is not None:
+            timing["a0"].record()
+        jcS, irS, pr, plan = fsparse.assemble(ii_d, jj_d, vals[0], t.m, t.n, prS=prS)
+        if timing is not None:
+            timing["a1"].record()
+        for r in range(NUMERIC_STEPS):
+            if timing is not None:
+                timing["n"][r][0].record()
+            fsparse.numeric(plan, vals[(r + 1) % 4], out)
+            if timing is not None:
+                timing["n"][r][1].record()
+        nnz = plan.nnz
+        plan.close()
+        return nnz
+
+    for _ in range(args.warmup):
+        nnz = step()
+    torch.cuda.synchronize()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
+    sampler = ClockSampler(gpu_index)
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    timings = [{"a0": mk(), "a1": mk(), "n": [(mk(), mk()) for _ in range(NUMERIC_STEPS)]}
+               for _ in range(args.steps)]
+    ev0, ev1 = mk(), mk()
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    n_launch0 = fsparse.fsparse_kernel_launches()
+    ev0.record()
+    for k in range(args.steps):
+        nnz = step(timings[k])
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = fsparse.fsparse_kernel_launches() - n_launch0
+    barrier(world)
+    clocks = sampler.stop()
+    local_ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(local_ms, world, dev)
+    full_ms = statistics.median([tm["a0"].elapsed_time(tm["a1"]) for tm in timings])
+    num_ms = [a.elapsed_time(b) for tm in timings for (a, b) in tm["n"]]
+    num_avg = statistics.mean(num_ms)
+
+    peak, peak_kind = hbm_peak()
+    B_num = 12 * L + 8 * nnz
+    B_full = 16 * L + 12 * nnz + 4 * (t.n + 1)
+    achieved = B_num / (num_avg / 1e3) / 1e9
+    src_hash = kernel_source_hash("numeric.cu")
+    traffic = profiled_traffic(f"numeric_kernel_{WORKLOAD}.md", src_hash)
+    value = world * L * (1 + NUMERIC_STEPS) / (ms / 1e3) / 1e9
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        h_ii = torch.from_numpy(t.ii).pin_memory()
+        h_jj = torch.from_numpy(t.jj).pin_memory()
+        h_vals = [torch.from_numpy(t.s).pin_memory()] + \
+                 [torch.from_numpy(inputs.mesh_values(L, sd)).pin_memory() for sd in VALUE_SEEDS[1:]]
+        h_out = torch.empty(L, dtype=torch.float64).pin_memory()
+        h_jc = torch.empty(t.n + 1, dtype=torch.int32).pin_memory()
+        h_ir = torch.empty(L, dtype=torch.int32).pin_memory()
+        d_s = torch.empty(L, dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            ii_d.copy_(h_ii, non_blocking=True)
+            jj_d.copy_(h_jj, non_blocking=True)
+            d_s.copy_(h_vals[0], non_blocking=True)
+            jcS, irS, pr, plan = fsparse.assemble(ii_d, jj_d, d_s, t.m, t.n, prS=prS)
+            h_jc.copy_(jcS, non_blocking=True)
+            h_ir[: plan.nnz].copy_(irS[: plan.nnz], non_blocking=True)
+            h_out[: plan.nnz].copy_(pr[: plan.nnz], non_blocking=True)
+            for r in range(NUMERIC_STEPS):
+                d_s.copy_(h_vals[(r + 1) % 4], non_blocking=True)
+                fsparse.numeric(plan, d_s, out)
+                h_out[: plan.nnz].copy_(out[: plan.nnz], non_blocking=True)
+            nz = plan.nnz
+            torch.cuda.synchronize()
+            plan.close()
+            return nz
+
+        e2e_step()
+        e_steps = max(3, args.steps // 3)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = mk(), mk()
+        e0.record()
+        for _ in range(e_steps):
+            nz = e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(e0.elapsed_time(e1) / e_steps, world, dev)
+        h2d = 8 * L + 8 * L * (1 + NUMERIC_STEPS)
+        d2h = 4 * (t.n + 1) + 12 * nz + 8 * nz * NUMERIC_STEPS
+        e2e = {"value": world * L * (1 + NUMERIC_STEPS) / (e_ms / 1e3) / 1e9, "unit": "G triplets/s",
+               "ms_per_step": e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": e_steps}
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_batch:
+        extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sec, Ls = oracle_job(t, 4, NUMERIC_STEPS)
+        cpu = {"value": Ls * (1 + NUMERIC_STEPS) / sec / 1e9, "unit": "G triplets/s", "cores": 1,
+               "kind": "oracle", "seconds": sec,
+               "sample": f"first {Ls} triplets (1/4 of the cube, element order): one oracle assembly "
+                         f"+ {NUMERIC_STEPS} oracle numeric passes, single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": "G triplets/s (full assembly + 50 numeric re-assemblies)",
+            "value": value, "unit": "G triplets/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(t), "numeric_steps": NUMERIC_STEPS,
+                       "nnz": nnz, "l2": "inputs larger than L2 (1.49 GB of triplets per assembly)",
+                       "launch": cfg, "parallelism": f"replicas{world}"},
+            "full": {"ms": full_ms, "gtps": L / full_ms / 1e6,
+                     "algorithmic_bytes": B_full, "hbm_frac": B_full / (full_ms / 1e3) / 1e9 / peak},
+            "numeric": {"ms": num_avg, "gtps": L / num_avg / 1e6, "algorithmic_bytes": B_num,
+                        "hbm_frac": achieved / peak},
+            "roofline": {"kernel": "numeric_kernel", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": B_num, "kernel_source_sha1": src_hash},
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * fsparse.h -- GB300-native Matlab-compatible sparse assembly
+ *              S = sparse(i, j, s, m, n, nzmax)
+ *
+ * Method: S. Engblom and D. Lukarski, "Fast Matlab compatible sparse assembly
+ * on multicore computers", arXiv:1406.1066.  Section numbers below refer to it.
+ *
+ * What the library computes (§1, §2.1, §2.2):
+ *   Input  (§2.2, input listing): unit-offset int32 row indices ii[len],
+ *          column indices jj[len], double values sr[len], dimensions m, n.
+ *   Output (§2.1, CCS arrays under Eq. (2.1)):
+ *          jcS[n+1]  column pointer, jcS[0] = 0, jcS[n] = nnz;
+ *          irS[nnz]  zero-offset rows, strictly ascending inside a column;
+ *          prS[nnz]  values; repeated (i, j) pairs are summed.
+ *   Intermediate (§2.2, Eqs. (2.2)-(2.3), "inverse rank"):
+ *          irank[len], irank[k] = CCS slot of triplet k,
+ *          irS[irank[k]] = ii[k] - 1, nnz = 1 + max irank.
+ *   Summation order (App. A post-processing, serial insert): every slot is
+ *          the fold (((+0.0 + sr[k0]) + sr[k1]) + ...) over its triplets in
+ *          ascending k.  Results are therefore deterministic to the bit and
+ *          independent of launch shape; a slot whose only inputs are -0.0
+ *          holds +0.0.
+ *   Explicit zeros: the pattern is defined by the indices alone (Eq. (2.2));
+ *          zero values and sums that cancel keep their slot.
+ *
+ * Conventions for every entry point:
+ *   * Array pointers are DEVICE pointers (cudaMalloc, cudaMallocAsync or a
+ *     framework allocator) unless a parameter name starts with h_.  The
+ *     caller owns them; the library never frees them.
+ *   * `stream` is a cudaStream_t passed as void*; 0 is the legacy default
+ *     stream.  All device work is enqueued on it.
+ *   * Sizes: the paper's indices are `int` (§2.2 listings); this library
+ *     accepts len and nzmax up to 2^30 - 1 (its scan words keep two flag
+ *     bits); larger -> FSPARSE_ERR_SIZE.
+ *   * Errors never abort, trap or assert on the device.  Device-side
+ *     findings (bad index, bounded wait expired) are written to a status
+ *     word that the host reads at the single synchronisation point of the
+ *     symbolic phase.  On error no plan is returned (*plan_out = NULL)
+ *     unless stated otherwise, and output arrays hold unspecified values.
+ *   * Entry points are thread-safe with respect to distinct plans.  Calls
+ *     on one plan that overlap on the GPU (different streams, no ordering)
+ *     are the caller's responsibility, like any other device buffer.
+ */
+#ifndef FSPARSE_H
+#define FSPARSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fsparse_status {
+    FSPARSE_OK = 0,
+    FSPARSE_ERR_ARG = 1,     /* NULL pointer, negative size/dimension, bad option  */
+    FSPARSE_ERR_INDEX = 2,   /* some index < 1, or > an explicit m / n (App. A)     */
+    FSPARSE_ERR_NZMAX = 3,   /* 0 < nzmax < nnz, or an output capacity below nnz    */
+    FSPARSE_ERR_SIZE = 4,    /* len, nzmax or a batch total beyond 2^30 - 1         */
+    FSPARSE_ERR_NOMEM = 5,   /* device allocation failed                           */
+    FSPARSE_ERR_CUDA = 6,    /* a CUDA runtime call failed (see last error string) */
+    FSPARSE_ERR_TIMEOUT = 7, /* a bounded device-side wait expired (no hang)       */
+    FSPARSE_ERR_INTERNAL = 8 /* a kernel's own index check failed (access skipped) */
+} fsparse_status;
+
+/* Opaque, library-owned symbolic result (the "quasi assembly" state of §2.1:
+   the information kept between repeated assemblies of one pattern). */
+typedef struct fsparse_plan_s *fsparse_plan;
+/* Opaque, library-owned concatenation of many plans for batched numerics. */
+typedef struct fsparse_batch_s *fsparse_batch;
+
+/* ------------------------------------------------------------------------
+ * Symbolic assembly (§2.2-§2.3: the intermediate format irank + jcS, plus
+ * irS, which Eq. (2.2) fixes from irank and ii).
+ *
+ *   ii, jj   device int32[len], unit-offset.  Read only.  May be NULL when
+ *            len == 0.
+ *   m, n     dimensions; 0 means implicit = the largest index (§2.2).
+ *   nzmax    0: capacity = nnz.  nzmax >= nnz: irS/prS capacity is nzmax,
+ *            slots [nnz, nzmax) hold irS = 0 / prS = +0.0 and jcS is
+ *            unaffected.  0 < nzmax < nnz: FSPARSE_ERR_NZMAX.  (The paper
+ *            names nzmax only in the call of §1; this is the reading used.)
+ *   plan_out receives a new plan on success.
+ *
+ * Synchronises `stream` once (to read nnz and the device status word).
+ * Allocates the plan's device arrays stream-ordered on `stream`.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_symbolic(const int32_t *ii, const int32_t *jj, int64_t len,
+                                int32_t m, int32_t n, int64_t nzmax,
+                                void *stream, fsparse_plan *plan_out);
+
+/* Dimensions and sizes of a plan.  Any output pointer may be NULL.
+   `cap` is the irS/prS capacity (nnz, or nzmax when larger).  Host only. */
+fsparse_status fsparse_plan_info(fsparse_plan plan, int32_t *m, int32_t *n, int64_t *len,
+                                 int64_t *nnz, int64_t *cap);
+
+/* Plan-owned device arrays, valid until fsparse_plan_destroy; read only for
+   the caller.  irank int32[len] (Eq. (2.2)), jcS int32[n+1], irS int32[cap].
+   Any output pointer may be NULL.  Host only. */
+fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank,
+                                   const int32_t **jcS, const int32_t **irS);
+
+/* Release a plan (NULL is a no-op).  Waits for outstanding device work that
+   may still read the plan's arrays. */
+fsparse_status fsparse_plan_destroy(fsparse_plan plan);
+
+/* ------------------------------------------------------------------------
+ * Numeric assembly (Eq. (2.3); App. A post-processing): prS[slot] is the
+ * ascending-k fold from +0.0 of sr[k] over the triplets of that slot.
+ *
+ *   sr   device double[len] in the triplet order of the symbolic call.
+ *   prS  device double[cap] (cap from fsparse_plan_info); fully written,
+ *        including the zero tail [nnz, cap).
+ *
+ * No synchronisation, no allocation, no validation of values: safe to call
+ * repeatedly on new values of one pattern (re-assembly in time-dependent
+ * nonlinear PDE solvers, §1) and to record into a CUDA graph.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_numeric(fsparse_plan plan, const double *sr, double *prS, void *stream);
+
+/* Adjoint (transpose) of the numeric map, which is linear in sr (Eq. (2.3)):
+   ds[k] = dprS[irank[k]] for k < len.  dprS device double[>= nnz], ds device
+   double[len].  Exact (a gather, no rounding).  No sync, no allocation. */
+fsparse_status fsparse_numeric_adjoint(fsparse_plan plan, const double *dprS, double *ds,
+                                       void *stream);
+
+/* ------------------------------------------------------------------------
+ * Full assembly: symbolic + numeric in one call, S = sparse(i,j,s,m,n,nzmax)
+ * of §1.  prS is caller-owned with `prS_capacity` doubles.  The CCS arrays
+ * jcS and irS are the returned plan's (fsparse_plan_arrays).
+ *
+ * When prS_capacity >= max(len, nzmax) the values are folded inside the
+ * symbolic pass; otherwise the numeric pass runs after nnz is known, and a
+ * capacity below the plan's cap returns FSPARSE_ERR_NZMAX WITH the plan
+ * (*plan_out set), so the caller can allocate and call fsparse_numeric.
+ * plan_out must not be NULL.  Synchronises `stream` once or twice.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const double *sr,
+                                int64_t len, int32_t m, int32_t n, int64_t nzmax,
+                                double *prS, int64_t prS_capacity, void *stream,
+                                fsparse_plan *plan_out);
+
+/* ------------------------------------------------------------------------
+ * Batched numeric re-assembly of many independent patterns (many small
+ * assemblies per time step).  The batch concatenates `count` plans: triplet
+ * k of plan b is element h_len_off[b] + k of the concatenated sr, and slot
+ * p < nnz_b of plan b is element h_nnz_off[b] + p of the concatenated prS,
+ * where the offsets are exclusive prefix sums of each plan's len and nnz
+ * (read them with fsparse_batch_info; zero tails from nzmax are not part of
+ * a batch).  The total len must stay below 2^30.  The plans may be destroyed
+ * after the batch is created.  Synchronises `stream` once.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, void *stream,
+                                    fsparse_batch *batch_out);
+
+/* Host offsets: h_len_off and h_nnz_off receive count+1 int64 each (either
+   may be NULL).  Host only. */
+fsparse_status fsparse_batch_info(fsparse_batch batch, int32_t *count, int64_t *h_len_off,
+                                  int64_t *h_nnz_off);
+
+/* All instances in ONE launch (a persistent kernel over the concatenated
+   triplet space); bit-identical to calling fsparse_numeric per plan.  No
+   sync, no allocation: capturable in a CUDA graph. */
+fsparse_status fsparse_batch_numeric(fsparse_batch batch, const double *sr_concat,
+                                     double *prS_concat, void *stream);
+
+fsparse_status fsparse_batch_destroy(fsparse_batch batch);
+
+/* ------------------------------------------------------------------------
+ * Launch configuration and autotuning (library-specific; the paper's
+ * method has no tuning knobs).
+ *
+ * strategy: FSPARSE_SORT_ONESWEEP = global stable LSD radix sort of the
+ * packed (column,row) keys, one kernel per digit with decoupled look-back;
+ * FSPARSE_SORT_BUCKET = one stable partition by the high column bits,
+ * then a shared-memory sort of each column bucket fused with run detection,
+ * jcS, irank and the value fold.  Both give bit-identical results.  A
+ * bucket that outgrows shared memory makes the library redo the call with
+ * ONESWEEP (same results, more time).
+ * ---------------------------------------------------------------------- */
+typedef enum fsparse_strategy {
+    FSPARSE_SORT_AUTO = 0,
+    FSPARSE_SORT_ONESWEEP = 1,
+    FSPARSE_SORT_BUCKET = 2
+} fsparse_strategy;
+
+typedef struct fsparse_config {
+    int32_t strategy;        /* fsparse_strategy                                 */
+    int32_t radix_bits;      /* ONESWEEP digit width, 6..8                       */
+    int32_t sweep_items;     /* ONESWEEP items per thread: 8, 12 or 16            */
+    int32_t sweep_threads;   /* ONESWEEP threads per block: 256 or 512            */
+    int32_t bucket_target;   /* BUCKET mean items per bucket, 1024..16384         */
+    int32_t numeric_tile;    /* positions per numeric tile: 1024, 2048 or 4096    */
+} fsparse_config;
+
+/* The configuration the library would use for this problem shape (pure host
+   computation; no device access).  Precedence: fsparse_set_config override,
+   then the tuned table, then built-in defaults. */
+fsparse_status fsparse_get_config(int64_t len, int32_t m, int32_t n, fsparse_config *out);
+
+/* Process-wide override (NULL clears it).  Fields <= 0 keep the value that
+   would otherwise apply.  Invalid values: FSPARSE_ERR_ARG.  Host only. */
+fsparse_status fsparse_set_config(const fsparse_config *cfg);
+
+/* Time every candidate configuration on the given device problem (the
+   inputs are only read) with CUDA events on `stream`, keep the fastest for
+   the problem's size class in the process-wide table, and report it in
+   *best (may be NULL).  `reps` timed runs per candidate (>= 1).  Allocates
+   and synchronises freely; not for use inside graph capture. */
+fsparse_status fsparse_autotune(const int32_t *ii, const int32_t *jj, const double *sr,
+                                int64_t len, int32_t m, int32_t n, int32_t reps,
+                                void *stream, fsparse_config *best);
+
+/* Persist / restore the tuned table as JSON (host files). */
+fsparse_status fsparse_tune_save(const char *path);
+fsparse_status fsparse_tune_load(const char *path);
+/* Forget every tuned entry (the override set by fsparse_set_config stays). */
+fsparse_status fsparse_tune_clear(void);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics.
+ * ---------------------------------------------------------------------- */
+/* Human-readable text of the last error raised on the calling thread. */
+const char *fsparse_last_error_string(void);
+/* Static name of a status code. */
+const char *fsparse_status_string(fsparse_status status);
+/* Number of kernels this library has launched in this process. */
+int64_t fsparse_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSPARSE_H */

@@ -1,0 +1,521 @@
+// api.cu -- the C ABI of libfsparse (declared in include/fsparse.h).
+//
+// Orchestration only: argument checks, plan allocation, choosing the sort
+// strategy, and the single host synchronisation of the symbolic phase.
+// Every step of the assembly itself runs in the kernels of onesweep.cu,
+// bucket.cu, scan.cu and numeric.cu.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+struct fsparse_plan_s {
+    fsp::Plan p;
+};
+struct fsparse_batch_s {
+    fsp::Batch b;
+};
+
+namespace fsp {
+
+std::atomic<int64_t> g_launches{0};
+static thread_local std::string g_err;
+
+fsparse_status set_error(fsparse_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+fsparse_status cuda_error(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? FSPARSE_ERR_NOMEM : FSPARSE_ERR_CUDA;
+}
+
+int sm_count(int) {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
+// Stream-ordered allocations come from the device's default memory pool;
+// keep freed blocks cached in the pool so repeated calls do not go back to
+// the driver.
+static fsparse_status ensure_pool(int dev) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64) return FSPARSE_OK;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return FSPARSE_OK;
+    cudaMemPool_t pool;
+    FSP_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t threshold = UINT64_MAX;
+    FSP_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
+    done[dev] = true;
+    return FSPARSE_OK;
+}
+
+fsparse_status device_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cuda_error(e, "cudaMallocAsync");
+    }
+    return FSPARSE_OK;
+}
+
+Scratch::~Scratch() {
+    for (int i = 0; i < n_; ++i) cudaFreeAsync(ptrs_[i], s_);
+}
+
+fsparse_status Scratch::alloc(void **p, size_t bytes) {
+    if (n_ == 32) return set_error(FSPARSE_ERR_NOMEM, "too many scratch buffers");
+    fsparse_status e = device_alloc(p, bytes, s_);
+    if (e == FSPARSE_OK) ptrs_[n_++] = *p;
+    return e;
+}
+
+// One pinned status block per host thread for the single readback.
+static DevStatus *host_status() {
+    static thread_local DevStatus *h = nullptr;
+    if (!h && cudaMallocHost(reinterpret_cast<void **>(&h), sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        h = nullptr;
+    }
+    return h;
+}
+
+static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) {
+    DevStatus *h = host_status();
+    if (!h) return set_error(FSPARSE_ERR_NOMEM, "cudaMallocHost failed");
+    FSP_CUDA(cudaMemcpyAsync(h, d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    FSP_CUDA(cudaStreamSynchronize(s));
+    *out = *h;
+    return FSPARSE_OK;
+}
+
+static void free_plan_arrays(Plan &p) {
+    cudaFree(p.irank);
+    cudaFree(p.jcS);
+    cudaFree(p.irS);
+    cudaFree(p.perm);
+    cudaFree(p.tile_slot0);
+    p.irank = p.jcS = p.irS = nullptr;
+    p.perm = p.tile_slot0 = nullptr;
+}
+
+constexpr int64_t kMaxLen = kMaxLookbackValue;   // 2^30 - 1
+
+static fsparse_status check_dims_args(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                                      int32_t n, int64_t nzmax) {
+    if (len < 0) return set_error(FSPARSE_ERR_ARG, "len < 0");
+    if (m < 0 || n < 0) return set_error(FSPARSE_ERR_ARG, "negative dimension");
+    if (nzmax < 0) return set_error(FSPARSE_ERR_ARG, "nzmax < 0");
+    if (len > 0 && (!ii || !jj)) return set_error(FSPARSE_ERR_ARG, "NULL index array");
+    if (len > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "len above 2^30 - 1");
+    if (nzmax > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "nzmax above 2^30 - 1");
+    return FSPARSE_OK;
+}
+
+// The sort + emit for one strategy; values folded into prS when given.
+static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const double *sr,
+                                   double *prS, int64_t len, Plan &plan, const fsparse_config &cfg,
+                                   DevStatus *d_st, Scratch &scratch, cudaStream_t s, bool *folded) {
+    *folded = false;
+    fsparse_status e;
+    if (cfg.strategy == FSPARSE_SORT_BUCKET && bucket_supported(len, plan.n, plan.key, cfg)) {
+        e = bucket_symbolic(ii, jj, sr, prS, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s);
+        if (e == FSPARSE_OK) *folded = sr != nullptr;
+        return e;
+    }
+    if ((e = onesweep_sort(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan.perm, d_st, scratch, s)) != FSPARSE_OK)
+        return e;
+    if ((e = emit_from_perm(ii, jj, len, plan.m, plan.n, plan.key, plan, d_st, scratch, s)) != FSPARSE_OK)
+        return e;
+    if (sr) {
+        e = launch_numeric(plan.perm, plan.tile_slot0, len, plan.ntiles, plan.numeric_tile, sr, prS,
+                           0, 0, s);
+        if (e == FSPARSE_OK) *folded = true;
+    }
+    return e;
+}
+
+// Symbolic phase with an optional fused fold into prS (capacity >= max(len, nzmax)).
+static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const double *sr,
+                                    double *prS, int64_t len, int32_t m, int32_t n, int64_t nzmax,
+                                    cudaStream_t s, Plan **out, const fsparse_config *force) {
+    *out = nullptr;
+    fsparse_status e = check_dims_args(ii, jj, len, m, n, nzmax);
+    if (e != FSPARSE_OK) return e;
+    int dev = 0;
+    FSP_CUDA(cudaGetDevice(&dev));
+    if ((e = ensure_pool(dev)) != FSPARSE_OK) return e;
+
+    Scratch scratch(s);
+    DevStatus *d_st = nullptr;
+    DevStatus h_st{};
+    if ((e = scratch.get(&d_st, 1)) != FSPARSE_OK) return e;
+    FSP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s));
+
+    if (m == 0 || n == 0) {   // implicit dimensions (§2.2): one extra synchronisation
+        if ((e = launch_minmax(ii, jj, len, m, n, d_st, s)) != FSPARSE_OK) return e;
+        if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return e;
+        if (h_st.bad_index) return set_error(FSPARSE_ERR_INDEX, "index below 1 or above its dimension");
+        if (m == 0) m = h_st.max_i;
+        if (n == 0) n = h_st.max_j;
+    }
+
+    Plan *plan = new (std::nothrow) Plan();
+    if (!plan) return set_error(FSPARSE_ERR_NOMEM, "host allocation");
+    plan->device = dev;
+    plan->m = m;
+    plan->n = n;
+    plan->len = len;
+    plan->key.rb = m > 0 ? bits_for((uint64_t)m - 1) : 0;
+    plan->key.cb = n > 0 ? bits_for((uint64_t)n - 1) : 0;
+    fsparse_config cfg = force ? *force : resolve_config(len, plan->key);
+    plan->cfg = cfg;
+    plan->numeric_tile = cfg.numeric_tile;
+    plan->ntiles = (len + cfg.numeric_tile - 1) / cfg.numeric_tile;
+    const int64_t irs_cap = std::max<int64_t>(std::max<int64_t>(len, nzmax), 1);
+
+    auto fail = [&](fsparse_status st) {
+        free_plan_arrays(*plan);
+        delete plan;
+        return st;
+    };
+    if ((e = device_alloc(reinterpret_cast<void **>(&plan->irank), (size_t)std::max<int64_t>(len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->perm), (size_t)std::max<int64_t>(len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->irS), (size_t)irs_cap * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->jcS), ((size_t)n + 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->tile_slot0), ((size_t)plan->ntiles + 1) * 4, s)))
+        return fail(e);
+
+    bool folded = false;
+    if (len == 0) {
+        if (cudaMemsetAsync(plan->jcS, 0, ((size_t)n + 1) * 4, s) != cudaSuccess ||
+            cudaMemsetAsync(plan->tile_slot0, 0, 4, s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+        folded = sr != nullptr;
+    } else {
+        e = run_symbolic(ii, jj, sr, prS, len, *plan, cfg, d_st, scratch, s, &folded);
+        if (e != FSPARSE_OK) return fail(e);
+    }
+    if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
+    if (h_st.overflow && !h_st.bad_index && !h_st.timeout) {
+        // A column bucket outgrew shared memory: same result through onesweep.
+        fsparse_config os = cfg;
+        os.strategy = FSPARSE_SORT_ONESWEEP;
+        plan->cfg = os;
+        if (cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+        e = run_symbolic(ii, jj, sr, prS, len, *plan, os, d_st, scratch, s, &folded);
+        if (e != FSPARSE_OK) return fail(e);
+        if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
+    }
+    if (h_st.bad_index) return fail(set_error(FSPARSE_ERR_INDEX, "index below 1 or above its dimension"));
+    if (h_st.timeout) return fail(set_error(FSPARSE_ERR_TIMEOUT, "device look-back wait expired"));
+    if (h_st.oob) return fail(set_error(FSPARSE_ERR_INTERNAL, "internal index check failed"));
+    const int64_t nnz = len ? (int64_t)h_st.nnz : 0;
+    if (nzmax > 0 && nzmax < nnz) return fail(set_error(FSPARSE_ERR_NZMAX, "nzmax below nnz"));
+    plan->nnz = nnz;
+    plan->cap = std::max(nnz, nzmax);
+    if (plan->cap > nnz) {
+        if ((e = launch_fill(plan->irS, folded ? prS : nullptr, nnz, plan->cap, s)) != FSPARSE_OK) return fail(e);
+    }
+    *out = plan;
+    return FSPARSE_OK;
+}
+
+}  // namespace fsp
+
+using namespace fsp;
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+fsparse_status fsparse_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                                int32_t n, int64_t nzmax, void *stream, fsparse_plan *plan_out) {
+    if (!plan_out) return set_error(FSPARSE_ERR_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    Plan *p = nullptr;
+    fsparse_status e = symbolic_impl(ii, jj, nullptr, nullptr, len, m, n, nzmax, as_stream(stream), &p, nullptr);
+    if (e != FSPARSE_OK) return e;
+    *plan_out = reinterpret_cast<fsparse_plan>(p);
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_plan_info(fsparse_plan plan, int32_t *m, int32_t *n, int64_t *len,
+                                 int64_t *nnz, int64_t *cap) {
+    if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
+    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    if (m) *m = p.m;
+    if (n) *n = p.n;
+    if (len) *len = p.len;
+    if (nnz) *nnz = p.nnz;
+    if (cap) *cap = p.cap;
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank, const int32_t **jcS,
+                                   const int32_t **irS) {
+    if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
+    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    if (irank) *irank = p.irank;
+    if (jcS) *jcS = p.jcS;
+    if (irS) *irS = p.irS;
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_plan_destroy(fsparse_plan plan) {
+    if (!plan) return FSPARSE_OK;
+    Plan *p = &reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    free_plan_arrays(*p);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_numeric(fsparse_plan plan, const double *sr, double *prS, void *stream) {
+    if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
+    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    if ((p.len > 0 && !sr) || (p.cap > 0 && !prS)) return set_error(FSPARSE_ERR_ARG, "NULL array");
+    return launch_numeric(p.perm, p.tile_slot0, p.len, p.ntiles, p.numeric_tile, sr, prS, p.nnz, p.cap,
+                          as_stream(stream));
+}
+
+fsparse_status fsparse_numeric_adjoint(fsparse_plan plan, const double *dprS, double *ds, void *stream) {
+    if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
+    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    if (p.len > 0 && (!dprS || !ds)) return set_error(FSPARSE_ERR_ARG, "NULL array");
+    return launch_adjoint(p.irank, p.len, dprS, ds, p.nnz, as_stream(stream));
+}
+
+fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
+                                int32_t m, int32_t n, int64_t nzmax, double *prS,
+                                int64_t prS_capacity, void *stream, fsparse_plan *plan_out) {
+    if (!plan_out) return set_error(FSPARSE_ERR_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (len > 0 && !sr) return set_error(FSPARSE_ERR_ARG, "NULL value array");
+    if (prS_capacity < 0 || (prS_capacity > 0 && !prS)) return set_error(FSPARSE_ERR_ARG, "bad prS");
+    cudaStream_t s = as_stream(stream);
+    Plan *p = nullptr;
+    fsparse_status e;
+    if (prS_capacity >= std::max<int64_t>(len, nzmax) && prS_capacity > 0) {
+        e = symbolic_impl(ii, jj, sr, prS, len, m, n, nzmax, s, &p, nullptr);
+        if (e != FSPARSE_OK) return e;
+        *plan_out = reinterpret_cast<fsparse_plan>(p);
+        return FSPARSE_OK;
+    }
+    e = symbolic_impl(ii, jj, nullptr, nullptr, len, m, n, nzmax, s, &p, nullptr);
+    if (e != FSPARSE_OK) return e;
+    *plan_out = reinterpret_cast<fsparse_plan>(p);
+    if (prS_capacity < p->cap) return set_error(FSPARSE_ERR_NZMAX, "prS capacity below the plan's cap");
+    return launch_numeric(p->perm, p->tile_slot0, p->len, p->ntiles, p->numeric_tile, sr, prS, p->nnz,
+                          p->cap, s);
+}
+
+// ---- batch ----------------------------------------------------------------
+fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, void *stream,
+                                    fsparse_batch *batch_out) {
+    if (!batch_out) return set_error(FSPARSE_ERR_ARG, "batch_out is NULL");
+    *batch_out = nullptr;
+    if (count < 0 || (count > 0 && !h_plans)) return set_error(FSPARSE_ERR_ARG, "bad plan list");
+    cudaStream_t s = as_stream(stream);
+    int64_t total_len = 0, total_nnz = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        if (!h_plans[b]) return set_error(FSPARSE_ERR_ARG, "NULL plan in batch");
+        const Plan &p = reinterpret_cast<fsparse_plan_s *>(h_plans[b])->p;
+        total_len += p.len;
+        total_nnz += p.nnz;
+    }
+    if (total_len > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "batch total len above 2^30 - 1");
+    Batch *bt = new (std::nothrow) Batch();
+    if (!bt) return set_error(FSPARSE_ERR_NOMEM, "host allocation");
+    cudaGetDevice(&bt->device);
+    bt->count = count;
+    bt->total_len = total_len;
+    bt->total_nnz = total_nnz;
+    bt->h_len_off = new (std::nothrow) int64_t[count + 1];
+    bt->h_nnz_off = new (std::nothrow) int64_t[count + 1];
+    bt->numeric_tile = 4096;
+    bt->ntiles = (total_len + bt->numeric_tile - 1) / bt->numeric_tile;
+    auto fail = [&](fsparse_status st) {
+        cudaFree(bt->perm);
+        cudaFree(bt->tile_slot0);
+        delete[] bt->h_len_off;
+        delete[] bt->h_nnz_off;
+        delete bt;
+        return st;
+    };
+    if (!bt->h_len_off || !bt->h_nnz_off) return fail(set_error(FSPARSE_ERR_NOMEM, "host allocation"));
+    fsparse_status e;
+    if ((e = device_alloc(reinterpret_cast<void **>(&bt->perm), (size_t)std::max<int64_t>(total_len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&bt->tile_slot0), ((size_t)bt->ntiles + 1) * 4, s)))
+        return fail(e);
+    int64_t lo = 0, no = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        const Plan &p = reinterpret_cast<fsparse_plan_s *>(h_plans[b])->p;
+        bt->h_len_off[b] = lo;
+        bt->h_nnz_off[b] = no;
+        if ((e = launch_batch_concat(p.perm, bt->perm + lo, p.len, (uint32_t)lo, s)) != FSPARSE_OK) return fail(e);
+        lo += p.len;
+        no += p.nnz;
+    }
+    bt->h_len_off[count] = lo;
+    bt->h_nnz_off[count] = no;
+    {
+        Scratch scratch(s);
+        uint32_t *counts = nullptr;
+        DevStatus *d_st = nullptr;
+        DevStatus h_st{};
+        if ((e = scratch.get(&counts, (size_t)bt->ntiles + 1)) != FSPARSE_OK) return fail(e);
+        if ((e = scratch.get(&d_st, 1)) != FSPARSE_OK) return fail(e);
+        if (cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+        if ((e = launch_tile_heads(bt->perm, total_len, bt->numeric_tile, counts, bt->ntiles, s)) != FSPARSE_OK)
+            return fail(e);
+        if ((e = exclusive_scan_u32(counts, bt->tile_slot0, bt->ntiles, d_st, scratch, s)) != FSPARSE_OK)
+            return fail(e);
+        if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
+        if (h_st.timeout) return fail(set_error(FSPARSE_ERR_TIMEOUT, "device look-back wait expired"));
+    }
+    *batch_out = reinterpret_cast<fsparse_batch>(bt);
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_batch_info(fsparse_batch batch, int32_t *count, int64_t *h_len_off,
+                                  int64_t *h_nnz_off) {
+    if (!batch) return set_error(FSPARSE_ERR_ARG, "batch is NULL");
+    const Batch &b = reinterpret_cast<fsparse_batch_s *>(batch)->b;
+    if (count) *count = b.count;
+    if (h_len_off) std::memcpy(h_len_off, b.h_len_off, sizeof(int64_t) * (b.count + 1));
+    if (h_nnz_off) std::memcpy(h_nnz_off, b.h_nnz_off, sizeof(int64_t) * (b.count + 1));
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_batch_numeric(fsparse_batch batch, const double *sr_concat, double *prS_concat,
+                                     void *stream) {
+    if (!batch) return set_error(FSPARSE_ERR_ARG, "batch is NULL");
+    const Batch &b = reinterpret_cast<fsparse_batch_s *>(batch)->b;
+    if (b.total_len > 0 && (!sr_concat || !prS_concat)) return set_error(FSPARSE_ERR_ARG, "NULL array");
+    return launch_numeric(b.perm, b.tile_slot0, b.total_len, b.ntiles, b.numeric_tile, sr_concat,
+                          prS_concat, b.total_nnz, b.total_nnz, as_stream(stream));
+}
+
+fsparse_status fsparse_batch_destroy(fsparse_batch batch) {
+    if (!batch) return FSPARSE_OK;
+    Batch *b = &reinterpret_cast<fsparse_batch_s *>(batch)->b;
+    cudaFree(b->perm);
+    cudaFree(b->tile_slot0);
+    delete[] b->h_len_off;
+    delete[] b->h_nnz_off;
+    delete b;
+    return FSPARSE_OK;
+}
+
+// ---- diagnostics ------------------------------------------------------------
+const char *fsparse_last_error_string(void) { return g_err.c_str(); }
+
+const char *fsparse_status_string(fsparse_status st) {
+    switch (st) {
+        case FSPARSE_OK: return "FSPARSE_OK";
+        case FSPARSE_ERR_ARG: return "FSPARSE_ERR_ARG";
+        case FSPARSE_ERR_INDEX: return "FSPARSE_ERR_INDEX";
+        case FSPARSE_ERR_NZMAX: return "FSPARSE_ERR_NZMAX";
+        case FSPARSE_ERR_SIZE: return "FSPARSE_ERR_SIZE";
+        case FSPARSE_ERR_NOMEM: return "FSPARSE_ERR_NOMEM";
+        case FSPARSE_ERR_CUDA: return "FSPARSE_ERR_CUDA";
+        case FSPARSE_ERR_TIMEOUT: return "FSPARSE_ERR_TIMEOUT";
+        case FSPARSE_ERR_INTERNAL: return "FSPARSE_ERR_INTERNAL";
+    }
+    return "FSPARSE_STATUS_UNKNOWN";
+}
+
+int64_t fsparse_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"
+
+// ---- autotuning (needs the internals above) -----------------------------------
+namespace fsp {
+void tune_store(int64_t len, const KeyLayout &key, const fsparse_config &cfg);
+std::vector<fsparse_config> tune_candidates(int64_t len, const KeyLayout &key);
+}  // namespace fsp
+
+extern "C" fsparse_status fsparse_autotune(const int32_t *ii, const int32_t *jj, const double *sr,
+                                           int64_t len, int32_t m, int32_t n, int32_t reps,
+                                           void *stream, fsparse_config *best) {
+    if (reps < 1 || m <= 0 || n <= 0) return set_error(FSPARSE_ERR_ARG, "autotune needs reps >= 1 and explicit m, n");
+    if (len <= 0 || !sr) return set_error(FSPARSE_ERR_ARG, "autotune needs a non-empty problem");
+    cudaStream_t s = as_stream(stream);
+    KeyLayout key;
+    key.rb = bits_for((uint64_t)m - 1);
+    key.cb = bits_for((uint64_t)n - 1);
+    double *prS = nullptr;
+    fsparse_status e;
+    if ((e = device_alloc(reinterpret_cast<void **>(&prS), (size_t)len * 8, s)) != FSPARSE_OK) return e;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best_ms = 1e30f;
+    fsparse_config best_cfg = resolve_config(len, key);
+    for (const fsparse_config &c : tune_candidates(len, key)) {
+        std::vector<float> times;
+        bool ok = true;
+        for (int r = 0; r < reps + 1 && ok; ++r) {   // first run warms the pool and caches
+            Plan *p = nullptr;
+            cudaEventRecord(t0, s);
+            e = symbolic_impl(ii, jj, sr, prS, len, m, n, 0, s, &p, &c);
+            cudaEventRecord(t1, s);
+            cudaEventSynchronize(t1);
+            if (e != FSPARSE_OK) {
+                ok = false;
+                break;
+            }
+            const bool fell_back = p->cfg.strategy != c.strategy;
+            fsparse_plan_destroy(reinterpret_cast<fsparse_plan>(p));
+            if (fell_back) {
+                ok = false;
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (r > 0) times.push_back(ms);
+        }
+        if (!ok) continue;
+        std::sort(times.begin(), times.end());
+        const float med = times[times.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            best_cfg = c;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFreeAsync(prS, s);
+    cudaStreamSynchronize(s);
+    if (best_ms >= 1e30f) return set_error(FSPARSE_ERR_CUDA, "no candidate configuration ran");
+    tune_store(len, key, best_cfg);
+    if (best) *best = best_cfg;
+    return FSPARSE_OK;
+}

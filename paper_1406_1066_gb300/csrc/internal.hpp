@@ -1,0 +1,153 @@
+// internal.hpp -- host-side types shared by the fsparse translation units.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fsparse.h"
+
+namespace fsp {
+
+struct DevStatus;
+
+// Number of bits needed for the values 0..x (0 for x == 0).
+inline int bits_for(uint64_t x) {
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+// Packed sort key of one triplet: ((j-1) << rb) | (i-1), column-major CCS order.
+struct KeyLayout {
+    int rb = 0;   // row bits, bits_for(m-1)
+    int cb = 0;   // column bits, bits_for(n-1)
+    int total() const { return rb + cb; }
+};
+
+// Everything the symbolic phase leaves behind (the reusable "quasi assembly"
+// state): the CCS pattern, the triplet->slot map and the sorted-order map
+// that drives the numeric fold.
+struct Plan {
+    int device = 0;
+    int32_t m = 0, n = 0;
+    int64_t len = 0, nnz = 0, cap = 0;
+    KeyLayout key;
+    int32_t *irank = nullptr;        // [len]
+    int32_t *jcS = nullptr;          // [n+1]
+    int32_t *irS = nullptr;          // [max(len, nzmax, 1)]
+    uint32_t *perm = nullptr;        // [len] sorted position -> k, kHeadBit on run heads
+    uint32_t *tile_slot0 = nullptr;  // [ntiles+1] slots before each numeric tile
+    int numeric_tile = 4096;
+    int64_t ntiles = 0;
+    fsparse_config cfg{};            // configuration that built this plan
+};
+
+struct Batch {
+    int device = 0;
+    int32_t count = 0;
+    int64_t total_len = 0, total_nnz = 0;
+    int64_t *h_len_off = nullptr;    // host [count+1]
+    int64_t *h_nnz_off = nullptr;    // host [count+1]
+    uint32_t *perm = nullptr;        // [total_len], k offset into the concatenation
+    uint32_t *tile_slot0 = nullptr;  // [ntiles+1]
+    int numeric_tile = 4096;
+    int64_t ntiles = 0;
+};
+
+// ---- errors ---------------------------------------------------------------
+fsparse_status set_error(fsparse_status st, const std::string &msg);
+fsparse_status cuda_error(cudaError_t e, const char *what);
+#define FSP_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::fsp::cuda_error(e_, #call);           \
+    } while (0)
+
+// ---- launch accounting -----------------------------------------------------
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+#define FSP_LAUNCHED()                                                        \
+    do {                                                                      \
+        ::fsp::count_launch();                                                \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) return ::fsp::cuda_error(e_, "kernel launch"); \
+    } while (0)
+
+int sm_count(int device);
+
+// ---- configuration ----------------------------------------------------------
+fsparse_config resolve_config(int64_t len, const KeyLayout &key);
+bool config_valid(const fsparse_config &c);
+fsparse_config default_config(int64_t len, const KeyLayout &key);
+
+// ---- stream-ordered scratch -------------------------------------------------
+// Allocations made during a call and released (stream-ordered) at its end.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    ~Scratch();
+    fsparse_status alloc(void **p, size_t bytes);
+    template <class T>
+    fsparse_status get(T **p, size_t count) {
+        return alloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    }
+
+  private:
+    cudaStream_t s_;
+    void *ptrs_[32] = {};
+    int n_ = 0;
+};
+
+fsparse_status device_alloc(void **p, size_t bytes, cudaStream_t s);
+
+// ---- kernel launchers (one per translation unit) ------------------------------
+// All return FSPARSE_OK or an error status; none synchronises.
+
+// Implicit dimensions and validation when m or n is zero.
+fsparse_status launch_minmax(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                             int32_t n, DevStatus *st, cudaStream_t s);
+
+// Global stable LSD radix sort (one kernel per digit) producing perm[len]
+// (sorted position -> k).  Tile/radix from cfg.
+fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                             int32_t n, const KeyLayout &key, const fsparse_config &cfg,
+                             uint32_t *perm_out, DevStatus *st, Scratch &scratch, cudaStream_t s);
+
+// Run detection + slots + irank + irS + column counts + numeric tile bases
+// from a sorted perm (gathering the keys back from ii/jj).
+fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                              int32_t n, const KeyLayout &key, Plan &plan, DevStatus *st,
+                              Scratch &scratch, cudaStream_t s);
+
+// Exclusive scan of counts[count] into out[count+1] (out[count] = total).
+fsparse_status exclusive_scan_u32(const uint32_t *counts, uint32_t *out, int64_t count,
+                                  DevStatus *st, Scratch &scratch, cudaStream_t s);
+
+// Numeric fold prS[slot] over perm/tile bases; tail [nnz, cap) zero-filled.
+fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *tile_slot0, int64_t len,
+                              int64_t ntiles, int tile, const double *sr, double *prS,
+                              int64_t nnz, int64_t cap, cudaStream_t s);
+fsparse_status launch_adjoint(const int32_t *irank, int64_t len, const double *dprS, double *ds,
+                              int64_t nnz, cudaStream_t s);
+fsparse_status launch_fill(int32_t *irS, double *prS, int64_t from, int64_t to, cudaStream_t s);
+fsparse_status launch_iota(uint32_t *perm, int64_t len, cudaStream_t s);
+fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t len,
+                                   uint32_t offset, cudaStream_t s);
+fsparse_status launch_tile_heads(const uint32_t *perm, int64_t len, int tile, uint32_t *counts,
+                                 int64_t ntiles, cudaStream_t s);
+
+// Hybrid column-bucket path.  Returns FSPARSE_OK and sets *overflow when a
+// bucket does not fit; the caller then redoes the call with onesweep.
+fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr,
+                               double *prS, int64_t len, int32_t m, int32_t n,
+                               const KeyLayout &key, const fsparse_config &cfg, Plan &plan,
+                               DevStatus *st, Scratch &scratch, cudaStream_t s);
+bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg);
+
+}  // namespace fsp

@@ -1,0 +1,80 @@
+// scan.cu -- single-pass exclusive scan with decoupled look-back.
+//
+// Used for the column pointer (Part 4 of §2.3: jcS is the running sum of
+// unique counts per column, jcS[0] = 0, jcS[n] = nnz) and for the bucket
+// offsets of the hybrid path.  Tiles are taken by atomic ticket; each tile
+// publishes its aggregate, then its inclusive prefix, in 32-bit look-back
+// words (values below 2^30).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace fsp {
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+    scan_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t count,
+                uint32_t *look, uint32_t *ticket, DevStatus *st) {
+    constexpr int TILE = THREADS * ITEMS;
+    __shared__ uint32_t s_scan[THREADS / 32 + 1];
+    __shared__ uint32_t s_tile, s_excl;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_tile = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t p0 = tile * TILE + (int64_t)tid * ITEMS;
+    uint32_t v[ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        v[i] = p0 + i < count ? in[p0 + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t tile_sum;
+    const uint32_t mine = block_exclusive_scan<THREADS>(sum, s_scan, &tile_sum);
+    if (tid == 0) {
+        uint32_t *word = look + tile;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            st_release(word, kFlagInc | tile_sum);
+        } else {
+            st_release(word, kFlagAgg | tile_sum);
+            excl = lookback_exclusive(look, 1, tile, st);
+            st_release(word, kFlagInc | (excl + tile_sum));
+        }
+        s_excl = excl;
+    }
+    __syncthreads();
+    uint32_t run = s_excl + mine;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int64_t p = p0 + i;
+        if (p < count) {
+            out[p] = run;
+            run += v[i];
+            if (p == count - 1) out[count] = run;
+        }
+    }
+}
+
+fsparse_status exclusive_scan_u32(const uint32_t *counts, uint32_t *out, int64_t count,
+                                  DevStatus *st, Scratch &scratch, cudaStream_t s) {
+    constexpr int THREADS = 256, ITEMS = 8, TILE = THREADS * ITEMS;
+    if (count == 0) {
+        FSP_CUDA(cudaMemsetAsync(out, 0, 4, s));
+        return FSPARSE_OK;
+    }
+    const int64_t ntiles = (count + TILE - 1) / TILE;
+    uint32_t *look, *ticket;
+    fsparse_status e;
+    if ((e = scratch.get(&look, (size_t)ntiles)) != FSPARSE_OK) return e;
+    if ((e = scratch.get(&ticket, 1)) != FSPARSE_OK) return e;
+    FSP_CUDA(cudaMemsetAsync(look, 0, (size_t)ntiles * 4, s));
+    FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
+    scan_kernel<THREADS, ITEMS><<<(unsigned)ntiles, THREADS, 0, s>>>(counts, out, count, look, ticket, st);
+    FSP_LAUNCHED();
+    return FSPARSE_OK;
+}
+
+}  // namespace fsp

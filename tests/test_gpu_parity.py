@@ -1,0 +1,184 @@
+"""CUDA path == oracle, element by element (irank, jcS, irS bit-exact; prS 0 ULP)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import pins
+from gpu_util import (DEV, assert_same, bits, check_against_oracle, check_properties, config,
+                      gpu_assemble, sampled_fold_check, to_dev)
+from paper_1406_1066_gb300 import fsparse, inputs
+
+pytestmark = pytest.mark.gpu
+
+STRATEGIES = [fsparse.SORT_ONESWEEP, fsparse.SORT_BUCKET]
+
+
+@pytest.fixture(params=STRATEGIES, ids=["onesweep", "bucket"])
+def strategy(request):
+    with config(strategy=request.param):
+        yield request.param
+
+
+def test_paper_examples(strategy):
+    g = pins.golden()
+    e = g["matrix_eq_2_1"]
+    for name in ("sorted_input", "running_example"):
+        t = g[name]
+        out = gpu_assemble(np.array(t["ii"], np.int32), np.array(t["jj"], np.int32),
+                           np.array(t["s"], np.float64))
+        assert out["irS"].tolist() == e["irS"] and out["jcS"].tolist() == e["jcS"]
+        assert out["prS"].tolist() == e["prS"]
+    assert out["irank"].tolist() == g["part4"]["irank"]
+
+
+@pytest.mark.parametrize("L", [1, 2, 31, 32, 33, 255, 2047, 2048, 2049, 4095, 4097, 8191, 70001])
+def test_ragged_random(strategy, L):
+    for c, (m, n) in enumerate([(7, 5), (300, 200), (5000, 3)]):
+        t = inputs.random_small(L, m, n, 1000 * L + c, dup=0.5)
+        if L > 4:
+            t.s[::5] = -0.0
+        check_against_oracle(t)
+
+
+def test_empty(strategy):
+    for m, n in [(3, 4), (0, 0), (1, 7)]:
+        e = np.zeros(0, np.int32)
+        g = gpu_assemble(e, e, np.zeros(0), m, n)
+        r = oracle.assemble(e, e, np.zeros(0), m, n)
+        assert_same(g, r)
+
+
+def test_single_cell_and_wide_keys(strategy):
+    t = inputs.random_small(5000, 1, 1, 3, dup=0.0)          # one key: one long run
+    check_against_oracle(t)
+    big = 2**30 - 1                                             # 30 + 30 key bits
+    t = inputs.random_small(100000, big, big, 4, dup=0.5)
+    check_against_oracle(t)
+    t = inputs.random_small(100000, 3, big, 5, dup=0.5)
+    check_against_oracle(t)
+    t = inputs.random_small(100000, big, 3, 6, dup=0.5)
+    check_against_oracle(t)
+
+
+def test_long_runs_across_tiles(strategy):
+    g = np.random.Generator(np.random.PCG64(8))
+    L = 300000
+    ii = np.where(g.random(L) < 0.7, 5, g.integers(1, 50, L)).astype(np.int32)
+    jj = np.where(ii == 5, 9, g.integers(1, 40, L)).astype(np.int32)
+    s = g.standard_normal(L)
+    t = inputs.Triplets(ii, jj, s, 50, 40)
+    check_against_oracle(t)
+
+
+def test_implicit_dims_and_nzmax(strategy):
+    t = inputs.random_small(20000, 900, 700, 12, dup=0.5)
+    g = gpu_assemble(t.ii, t.jj, t.s)
+    r = oracle.assemble(t.ii, t.jj, t.s)
+    assert_same(g, r)
+    r0 = oracle.assemble(t.ii, t.jj, t.s, 900, 700)
+    g = gpu_assemble(t.ii, t.jj, t.s, 900, 700, r0.nnz + 1000)
+    assert_same(g, oracle.assemble(t.ii, t.jj, t.s, 900, 700, r0.nnz + 1000))
+    with pytest.raises(fsparse.FsparseError) as e:
+        gpu_assemble(t.ii, t.jj, t.s, 900, 700, r0.nnz - 1)
+    assert e.value.status == fsparse.ERR_NZMAX
+
+
+def test_bad_indices(strategy):
+    t = inputs.random_small(5000, 40, 40, 2)
+    for mutate in ("zero_i", "neg_j", "big_i", "big_j"):
+        ii, jj = t.ii.copy(), t.jj.copy()
+        if mutate == "zero_i":
+            ii[1234] = 0
+        elif mutate == "neg_j":
+            jj[77] = -5
+        elif mutate == "big_i":
+            ii[4999] = 41
+        else:
+            jj[0] = 41
+        with pytest.raises(fsparse.FsparseError) as e:
+            gpu_assemble(ii, jj, t.s, 40, 40)
+        assert e.value.status == fsparse.ERR_INDEX
+        if mutate.startswith("big"):   # implicit dimensions simply grow
+            g = gpu_assemble(ii, jj, t.s)
+            assert_same(g, oracle.assemble(ii, jj, t.s))
+        else:
+            with pytest.raises(fsparse.FsparseError) as e:
+                gpu_assemble(ii, jj, t.s)
+            assert e.value.status == fsparse.ERR_INDEX
+
+
+def test_nonfinite_and_signed_zero(strategy):
+    ii = np.array([1, 1, 2, 2, 3, 3, 4], np.int32)
+    jj = np.array([1, 1, 1, 1, 2, 2, 2], np.int32)
+    s = np.array([np.inf, -np.inf, np.nan, 1.0, -0.0, -0.0, -0.0])
+    g = gpu_assemble(ii, jj, s, 4, 2)
+    r = oracle.assemble(ii, jj, s, 4, 2)
+    assert np.isnan(g["prS"][0]) and np.isnan(g["prS"][1])
+    assert bits(g["prS"][2:]).tolist() == bits(r.prS[2:]).tolist() == bits([0.0, 0.0]).tolist()
+
+
+@pytest.mark.parametrize("radix", [6, 7, 8])
+@pytest.mark.parametrize("shape", [(256, 8), (256, 12), (256, 16), (512, 8), (512, 12), (512, 16)])
+def test_onesweep_variants(radix, shape):
+    t = inputs.mesh3d(11, 21)
+    u = inputs.random_small(50000, 3000, 2000, 22, dup=0.4)
+    with config(strategy=fsparse.SORT_ONESWEEP, radix_bits=radix, sweep_threads=shape[0],
+                sweep_items=shape[1]):
+        check_against_oracle(t)
+        check_against_oracle(u)
+
+
+@pytest.mark.parametrize("tile", [1024, 2048, 4096])
+def test_numeric_tiles(strategy, tile):
+    t = inputs.mesh3d(13, 31)
+    with config(numeric_tile=tile):
+        g, r = check_against_oracle(t)
+        plan = g["plan"]
+        for seed in (1, 2):
+            s2 = inputs.mesh_values(t.L, seed)
+            pr = fsparse.numeric(plan, to_dev(s2)).cpu().numpy()
+            assert np.array_equal(bits(pr), bits(oracle.numeric(r.irank, s2, r.nnz)))
+
+
+def test_mesh2d_64(strategy):
+    t = inputs.workload("mesh2d_64")
+    g, r = check_against_oracle(t)
+    assert r.nnz == pins.mesh_nnz(64, 2) == 28162
+
+
+def test_uniform_1e6(strategy):
+    check_against_oracle(inputs.workload("uniform_1e6"))
+
+
+def test_pooled_2e4(strategy):
+    g, r = check_against_oracle(inputs.workload("pooled_2e4"))
+    assert r.nnz <= 2 * 10**6
+
+
+def test_mesh3d_60_full_and_numeric(strategy):
+    t = inputs.workload("mesh3d_60")
+    g, r = check_against_oracle(t)
+    assert r.nnz == pins.mesh_nnz(60, 3) == 3154318
+    s2 = inputs.mesh_values(t.L, 99)
+    pr = fsparse.numeric(g["plan"], to_dev(s2)).cpu().numpy()
+    assert np.array_equal(bits(pr), bits(oracle.numeric(r.irank, s2, r.nnz)))
+    g2 = gpu_assemble(t.ii, t.jj, t.s, t.m, t.n)   # determinism: run again, same bits
+    assert np.array_equal(g2["irank"], g["irank"]) and np.array_equal(bits(g2["prS"]), bits(g["prS"]))
+
+
+def test_mesh3d_100_properties(strategy):
+    """The 93M-triplet cube at full size, launched exactly as the benchmark does."""
+    t = inputs.workload("mesh3d_100")
+    ii_d, jj_d, s_d = to_dev(t.ii), to_dev(t.jj), to_dev(t.s)
+    jcS, irS, prS, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n)
+    check_properties(ii_d, jj_d, plan, expect_nnz=pins.mesh_nnz(100, 3))
+    assert plan.nnz == 14761198
+    sampled_fold_check(plan, t.s, prS, samples=1500, seed=1)
+    for seed in (1410, 1411, 1412):
+        s2 = inputs.mesh_values(t.L, seed)
+        pr = fsparse.numeric(plan, to_dev(s2))
+        sampled_fold_check(plan, s2, pr, samples=500, seed=seed)
+    del ii_d, jj_d, s_d, prS
+    plan.close()
+    torch.cuda.empty_cache()
