@@ -265,7 +265,7 @@ def gpu_arm(args):
     def to_dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
-    t = inputs.workload(WORKLOAD)
+    t = inputs.workload(args.workload) if args.workload != WORKLOAD else inputs.workload(WORKLOAD)
     L = t.L
     ii_d, jj_d = to_dev(t.ii), to_dev(t.jj)
     vals = [to_dev(t.s)] + [to_dev(inputs.mesh_values(L, sd)) for sd in VALUE_SEEDS[1:]]
@@ -323,12 +323,12 @@ def gpu_arm(args):
     B_full = 16 * L + 12 * nnz + 4 * (t.n + 1)
     achieved = B_num / (num_avg / 1e3) / 1e9
     src_hash = kernel_source_hash("numeric.cu")
-    traffic = profiled_traffic(f"numeric_kernel_{WORKLOAD}.md", src_hash)
+    traffic = profiled_traffic(f"numeric_kernel_{args.workload}.md", src_hash)
     value = world * L * (1 + NUMERIC_STEPS) / (ms / 1e3) / 1e9
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         h_ii = torch.from_numpy(t.ii).pin_memory()
         h_jj = torch.from_numpy(t.jj).pin_memory()
         h_vals = [torch.from_numpy(t.s).pin_memory()] + \
@@ -378,7 +378,7 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        sec, Ls = oracle_job(t, 4, NUMERIC_STEPS)
+        sec, Ls = oracle_job(t, 4 if t.L > 10**7 else 1, NUMERIC_STEPS)
         cpu = {"value": Ls * (1 + NUMERIC_STEPS) / sec / 1e9, "unit": "G triplets/s", "cores": 1,
                "kind": "oracle", "seconds": sec,
                "sample": f"first {Ls} triplets (1/4 of the cube, element order): one oracle assembly "
@@ -390,7 +390,8 @@ def gpu_arm(args):
             "value": value, "unit": "G triplets/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(t), "numeric_steps": NUMERIC_STEPS,
+            "config": {"workload": workload_desc(t), "workload_name": t.name,
+                       "numeric_steps": NUMERIC_STEPS,
                        "nnz": nnz, "l2": "inputs larger than L2 (1.49 GB of triplets per assembly)",
                        "launch": cfg, "parallelism": f"replicas{world}"},
             "full": {"ms": full_ms, "gtps": L / full_ms / 1e6,
@@ -422,6 +423,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="mesh3d_100 (default), or mesh3d_<N> for a smaller cube (profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

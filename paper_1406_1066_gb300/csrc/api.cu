@@ -110,12 +110,23 @@ static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) 
     return FSPARSE_OK;
 }
 
+// Release device arrays that kernels may still be reading: wait for the
+// device first (a plan may be used on any stream), then hand the blocks
+// back to the stream-ordered pool.
+static void release_device(void *const *ptrs, int count) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) any |= ptrs[i] != nullptr;
+    if (!any) return;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < count; ++i)
+        if (ptrs[i]) cudaFreeAsync(ptrs[i], nullptr);
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+}
+
 static void free_plan_arrays(Plan &p) {
-    cudaFree(p.irank);
-    cudaFree(p.jcS);
-    cudaFree(p.irS);
-    cudaFree(p.perm);
-    cudaFree(p.tile_slot0);
+    void *ptrs[5] = {p.irank, p.jcS, p.irS, p.perm, p.tile_slot0};
+    release_device(ptrs, 5);
     p.irank = p.jcS = p.irS = nullptr;
     p.perm = p.tile_slot0 = nullptr;
 }
@@ -361,8 +372,8 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
     bt->numeric_tile = 4096;
     bt->ntiles = (total_len + bt->numeric_tile - 1) / bt->numeric_tile;
     auto fail = [&](fsparse_status st) {
-        cudaFree(bt->perm);
-        cudaFree(bt->tile_slot0);
+        void *ptrs[2] = {bt->perm, bt->tile_slot0};
+        release_device(ptrs, 2);
         delete[] bt->h_len_off;
         delete[] bt->h_nnz_off;
         delete bt;
@@ -426,8 +437,12 @@ fsparse_status fsparse_batch_numeric(fsparse_batch batch, const double *sr_conca
 fsparse_status fsparse_batch_destroy(fsparse_batch batch) {
     if (!batch) return FSPARSE_OK;
     Batch *b = &reinterpret_cast<fsparse_batch_s *>(batch)->b;
-    cudaFree(b->perm);
-    cudaFree(b->tile_slot0);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != b->device) cudaSetDevice(b->device);
+    void *ptrs[2] = {b->perm, b->tile_slot0};
+    release_device(ptrs, 2);
+    if (cur != b->device) cudaSetDevice(cur);
     delete[] b->h_len_off;
     delete[] b->h_nnz_off;
     delete b;

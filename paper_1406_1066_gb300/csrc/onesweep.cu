@@ -255,11 +255,7 @@ template <int R, int THREADS, int ITEMS>
 static fsparse_status run_pass(const PassArgs &a, int64_t ntiles, cudaStream_t s) {
     using S = PassSmem<R, THREADS, ITEMS>;
     auto kern = onesweep_pass_kernel<R, THREADS, ITEMS>;
-    static bool attr = false;
-    if (!attr) {
-        FSP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes));
-        attr = true;
-    }
+    FSP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes));
     kern<<<(unsigned)ntiles, THREADS, S::bytes, s>>>(a);
     FSP_LAUNCHED();
     return FSPARSE_OK;

