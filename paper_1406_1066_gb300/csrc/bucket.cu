@@ -1,15 +1,489 @@
-// bucket.cu -- hybrid column-bucket path (placeholder until implemented).
+// bucket.cu -- the hybrid path: one partition by high column bits, then one
+// shared-memory sort per column bucket with everything else fused.
+//
+// The paper (§2.3) orders the triplets with counting passes whose tables are
+// as long as the matrix is wide or tall.  On a GPU the cheap counting pass is
+// the one whose table fits in shared memory, so the column index is split:
+//
+//   bucket = (j-1) >> cs            (up to 32768 buckets, 2^cs columns each)
+//
+//   1. count:    every block counts bucket sizes over its contiguous slice of
+//                jj in a shared-memory table;
+//   2. offsets:  per-bucket prefix over blocks, then an exclusive scan over
+//                buckets gives each (block, bucket) its output range;
+//   3. scatter:  every block re-reads its slice of ii/jj and appends packed
+//                words  (j-1 low bits | i-1 | k)  to its ranges -- one 8-byte
+//                write per triplet, the only global reordering pass;
+//   4. emit:     one CTA per bucket (taken by atomic ticket) loads the bucket,
+//                compresses the row range, sorts (column, row) with a stable
+//                LSD radix sort in shared memory (rank.cuh), puts
+//                each run of equal keys back into ascending k (the scatter
+//                keeps no order inside a block), detects runs by comparing
+//                neighbours (the collision detection of Part 3), numbers the
+//                slots with one decoupled look-back across buckets, and writes
+//                perm, irank, irS, jcS (Part 4's prefix, per bucket column),
+//                the numeric tile bases and -- in a full assembly -- prS by
+//                folding each run from +0.0 in ascending k.
+//
+// A bucket above the kernel's capacity, or a run longer than kRunSortMax,
+// sets DevStatus::overflow; the host then redoes the call with the global
+// onesweep sort, which has no such limit.  Results are identical either way.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.hpp"
+#include "rank.cuh"
 
 namespace fsp {
 
-bool bucket_supported(int64_t, int32_t, const KeyLayout &, const fsparse_config &) { return false; }
+constexpr int64_t kMaxBuckets = 32768;
+constexpr int kMaxColBits = 12;     // 2^cs column counters in shared memory
+constexpr int kRunSortMax = 128;    // longest run re-sorted by one thread
 
-fsparse_status bucket_symbolic(const int32_t *, const int32_t *, const double *, double *, int64_t,
-                               int32_t, int32_t, const KeyLayout &, const fsparse_config &, Plan &,
-                               DevStatus *, Scratch &, cudaStream_t) {
-    return set_error(FSPARSE_ERR_ARG, "bucket path unavailable");
+struct BucketShape {
+    int cs = 0;        // low column bits kept inside a bucket
+    int64_t nb = 0;    // number of buckets
+    int kb = 1;        // bits of k in a packed word
+    int grid = 1;      // blocks of the count/scatter kernels
+    int variant = 0;   // 0: 256 threads x 16 (4096 items), 1: 512 x 16 (8192 items)
+};
+
+static int shape_variant(int target) { return target <= 3000 ? 0 : 1; }
+
+static bool bucket_shape(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg,
+                         BucketShape *out) {
+    if (len <= 0 || n <= 0) return false;
+    BucketShape sh;
+    sh.kb = std::max(1, bits_for((uint64_t)len - 1));
+    const double per_col = (double)len / (double)n;
+    while (sh.cs < key.cb && per_col * (double)(1ll << (sh.cs + 1)) <= cfg.bucket_target) ++sh.cs;
+    sh.nb = ((int64_t)(n - 1) >> sh.cs) + 1;
+    while (sh.nb > kMaxBuckets && sh.cs < key.cb) {
+        ++sh.cs;
+        sh.nb = ((int64_t)(n - 1) >> sh.cs) + 1;
+    }
+    if (sh.nb > kMaxBuckets || sh.cs > kMaxColBits) return false;
+    if (sh.cs + key.rb + sh.kb > 64) return false;
+    sh.variant = shape_variant(cfg.bucket_target);
+    if (out) *out = sh;
+    return true;
+}
+
+bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg) {
+    return bucket_shape(len, n, key, cfg, nullptr);
+}
+
+// ----------------------------------------------------------------------------
+// 1. per-block bucket counts over a contiguous slice of jj.
+__global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len, int32_t n, int cs,
+                                    int nb, uint32_t *__restrict__ hist, DevStatus *st) {
+    extern __shared__ uint32_t s_h[];
+    const int tid = threadIdx.x;
+    for (int b = tid; b < nb; b += blockDim.x) s_h[b] = 0;
+    __syncthreads();
+    const int64_t g = blockIdx.x, G = gridDim.x;
+    const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
+    for (int64_t k = c0 + tid; k < c1; k += blockDim.x)
+        atomicAdd(&s_h[(uint32_t)(checked_index(jj[k], n, st) - 1) >> cs], 1u);
+    __syncthreads();
+    for (int b = tid; b < nb; b += blockDim.x) hist[g * nb + b] = s_h[b];
+}
+
+// 2a. offsets of each block inside each bucket, and bucket totals.
+__global__ void bucket_colprefix_kernel(const uint32_t *__restrict__ hist, uint32_t *__restrict__ goff,
+                                        uint32_t *__restrict__ tot, int nb, int G) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    uint32_t run = 0;
+    for (int g = 0; g < G; ++g) {
+        const uint32_t v = hist[(int64_t)g * nb + b];
+        goff[(int64_t)g * nb + b] = run;
+        run += v;
+    }
+    tot[b] = run;
+}
+
+// 3. scatter packed words into the buckets (order inside a block's range is
+//    not kept; the emit kernel restores ascending k inside each run).
+__global__ void bucket_scatter_kernel(const int32_t *__restrict__ ii, const int32_t *__restrict__ jj,
+                                      int64_t len, int32_t m, int32_t n, int rb, int cs, int kb,
+                                      int nb, const uint32_t *__restrict__ goff,
+                                      const uint32_t *__restrict__ bstart, uint64_t *__restrict__ words,
+                                      DevStatus *st) {
+    extern __shared__ uint32_t s_cur[];
+    const int tid = threadIdx.x;
+    const int64_t g = blockIdx.x, G = gridDim.x;
+    for (int b = tid; b < nb; b += blockDim.x) s_cur[b] = bstart[b] + goff[g * nb + b];
+    __syncthreads();
+    const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
+    const uint64_t lowmask = (1ull << cs) - 1;
+    for (int64_t k = c0 + tid; k < c1; k += blockDim.x) {
+        const uint32_t i0 = (uint32_t)(checked_index(ii[k], m, st) - 1);
+        const uint32_t j0 = (uint32_t)(checked_index(jj[k], n, st) - 1);
+        const uint32_t pos = atomicAdd(&s_cur[j0 >> cs], 1u);
+        const uint64_t w = ((uint64_t)(j0 & lowmask) << (rb + kb)) | ((uint64_t)i0 << kb) | (uint64_t)k;
+        if (in_range(pos, len, st)) words[pos] = w;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// 4. per-bucket sort + emit (+ fold).
+struct BucketEmitArgs {
+    const uint64_t *words;
+    const uint32_t *bstart;
+    int64_t nb;
+    int cs, rb, kb;
+    int32_t n;
+    int64_t len;
+    const double *sr;      // NULL: symbolic only
+    double *prS;
+    uint32_t *perm;
+    int32_t *irank, *irS, *jcS;
+    uint32_t *tile_slot0;
+    int num_shift;
+    int64_t ntiles_num;
+    uint32_t *look;
+    uint32_t *ticket;
+    DevStatus *st;
+};
+
+template <int THREADS, int IPT>
+struct BucketSmem {
+    static constexpr int CAP = THREADS * IPT, WARPS = THREADS / 32;
+    static constexpr size_t off_wcnt = (size_t)CAP * 8;
+    static constexpr size_t off_wm = off_wcnt + (size_t)WARPS * 256 * 4;
+    static constexpr size_t off_col = off_wm + (size_t)WARPS * 256 * 4;
+    static constexpr size_t off_local = off_col + (size_t)(1 << kMaxColBits) * 4;
+    static constexpr size_t off_scan = off_local + 256 * 4;
+    static constexpr size_t off_misc = off_scan + (WARPS + 2) * 4;
+    static constexpr size_t off_hpos = off_misc + 16 * 4;
+    static constexpr size_t bytes = off_hpos + ((size_t)(CAP + 1) * 2 + 15) / 16 * 16;
+};
+
+__device__ __forceinline__ int bits_of(uint32_t v) { return v ? 32 - __clz(v) : 0; }
+
+template <int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) {
+    using S = BucketSmem<THREADS, IPT>;
+    constexpr int CAP = S::CAP, WARPS = S::WARPS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_w = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_wcnt = reinterpret_cast<uint32_t *>(smem + S::off_wcnt);
+    uint32_t *s_wm = reinterpret_cast<uint32_t *>(smem + S::off_wm);
+    uint32_t *s_col = reinterpret_cast<uint32_t *>(smem + S::off_col);
+    uint32_t *s_local = reinterpret_cast<uint32_t *>(smem + S::off_local);
+    uint32_t *s_scan = reinterpret_cast<uint32_t *>(smem + S::off_scan);
+    uint32_t *s_misc = reinterpret_cast<uint32_t *>(smem + S::off_misc);
+    uint16_t *s_hpos = reinterpret_cast<uint16_t *>(smem + S::off_hpos);
+    double *s_val = reinterpret_cast<double *>(smem);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_misc[0] = atomicAdd(a.ticket, 1u);
+        s_misc[1] = 0xffffffffu;   // row min
+        s_misc[2] = 0;             // row max
+    }
+    __syncthreads();
+    const int64_t x = s_misc[0];
+    const int64_t b0 = a.bstart[x];
+    const int nx = (int)((int64_t)a.bstart[x + 1] - b0);
+    const int64_t col0 = x << a.cs;
+    const int ncols = (int)min64((int64_t)1 << a.cs, (int64_t)a.n - col0);
+    const int kb = a.kb, rb = a.rb;
+    const uint64_t kmask = (1ull << kb) - 1;
+
+    if (nx > CAP || nx < 0) {   // does not fit: flag it, keep the look-back chain moving
+        if (tid == 0) {
+            atomicOr(&a.st->overflow, 1u);
+            if (x == 0) {
+                st_release(a.look, kFlagInc);
+            } else {
+                st_release(a.look + x, kFlagAgg);
+                const uint32_t e = lookback_exclusive(a.look, 1, x, a.st);
+                st_release(a.look + x, kFlagInc | e);
+            }
+        }
+        return;
+    }
+
+    // Load the bucket (warp-striped) and find its row range.
+    uint64_t pk[IPT];
+    bool valid[IPT];
+    uint32_t rmin = 0xffffffffu, rmax = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int p = warp * 32 * IPT + i * 32 + lane;
+        valid[i] = p < nx;
+        pk[i] = 0;
+        if (valid[i]) {
+            pk[i] = a.words[b0 + p];
+            const uint32_t row = (uint32_t)((pk[i] >> kb) & ((1ull << rb) - 1));
+            rmin = min(rmin, row);
+            rmax = max(rmax, row);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        rmin = min(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+        rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    }
+    if (lane == 0) {
+        atomicMin(&s_misc[1], rmin);
+        atomicMax(&s_misc[2], rmax);
+    }
+    __syncthreads();
+    const uint32_t row_lo = nx ? s_misc[1] : 0u;
+    const int rbits = bits_of(nx ? s_misc[2] - row_lo : 0u);
+    const int npass = (a.cs + rbits + 7) / 8;
+    // Sort key inside the bucket: (column low bits, row - row_lo), then k below it.
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        if (valid[i]) {
+            const uint64_t w = pk[i];
+            const uint64_t row = ((w >> kb) & ((1ull << rb) - 1)) - row_lo;
+            const uint64_t lowcol = w >> (kb + rb);
+            pk[i] = ((((lowcol << rbits) | row)) << kb) | (w & kmask);
+        }
+    }
+
+    // Stable LSD radix sort of the sort key, 8 bits per pass, in shared memory.
+    for (int t = tid; t < WARPS * 256; t += THREADS) s_wm[t] = 0;
+    for (int d = 0; d < npass; ++d) {
+        for (int t = tid; t < WARPS * 256; t += THREADS) s_wcnt[t] = 0;
+        __syncthreads();
+        uint32_t dig[IPT], rnk[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) dig[i] = (uint32_t)(pk[i] >> (kb + 8 * d)) & 255u;
+        warp_rank<8, IPT>(dig, valid, s_wcnt + warp * 256, s_wm + warp * 256, rnk);
+        __syncthreads();
+        digit_offsets<8, THREADS>(s_wcnt, s_local, s_scan);
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            if (valid[i]) {
+                const uint32_t q = s_local[dig[i]] + s_wcnt[warp * 256 + dig[i]] + rnk[i];
+                if (in_range(q, nx, a.st)) s_w[q] = pk[i];
+            }
+        }
+        __syncthreads();
+        if (d + 1 < npass) {
+#pragma unroll
+            for (int i = 0; i < IPT; ++i)
+                if (valid[i]) pk[i] = s_w[warp * 32 * IPT + i * 32 + lane];
+            __syncthreads();
+        }
+    }
+    if (npass == 0) {
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+            if (valid[i]) s_w[warp * 32 * IPT + i * 32 + lane] = pk[i];
+        __syncthreads();
+    }
+
+    // Runs: a new run starts where the sort key changes (blocked positions).
+    const int pbase = tid * IPT;
+    uint32_t hmask = 0;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int p = pbase + i;
+        if (p < nx) {
+            const uint64_t sk = s_w[p] >> kb;
+            if (p == 0 || sk != (s_w[p - 1] >> kb)) hmask |= 1u << i;
+        }
+    }
+    uint32_t U;
+    const uint32_t hexcl = block_exclusive_scan<THREADS>(__popc(hmask), s_scan, &U);
+    if (tid == 0) st_release(a.look + x, (x == 0 ? kFlagInc : kFlagAgg) | U);
+    {
+        uint32_t h = hexcl;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+            if ((hmask >> i) & 1u) s_hpos[h++] = (uint16_t)(pbase + i);
+    }
+    if (tid == 0) s_hpos[U] = (uint16_t)nx;
+    for (int c = tid; c < (1 << a.cs); c += THREADS) s_col[c] = 0;
+    __syncthreads();
+
+    // Ascending k inside every run (the scatter kept no order within a block).
+    for (uint32_t h = tid; h < U; h += THREADS) {
+        const int lo = s_hpos[h], hi = s_hpos[h + 1];
+        if (hi - lo > kRunSortMax) {
+            atomicOr(&a.st->overflow, 1u);
+            continue;
+        }
+        for (int p = lo + 1; p < hi; ++p) {
+            const uint64_t v = s_w[p];
+            int q = p - 1;
+            while (q >= lo && s_w[q] > v) {
+                s_w[q + 1] = s_w[q];
+                --q;
+            }
+            s_w[q + 1] = v;
+        }
+    }
+    if (tid == 0) {
+        uint32_t e = 0;
+        if (x > 0) {
+            e = lookback_exclusive(a.look, 1, x, a.st);
+            st_release(a.look + x, kFlagInc | (e + U));
+        }
+        s_misc[3] = e;
+    }
+    __syncthreads();
+    const uint32_t E = s_misc[3];
+
+    // perm, irank, irS, column counts, numeric tile bases.
+    const uint64_t rmaskx = (1ull << rbits) - 1;
+    const uint32_t tile_mask = (1u << a.num_shift) - 1;
+    uint32_t slot = E + hexcl - 1;
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+        const int p = pbase + i;
+        if (p >= nx) continue;
+        const uint64_t v = s_w[p];
+        const uint32_t k = (uint32_t)(v & kmask);
+        const uint64_t sk = v >> kb;
+        const bool head = (hmask >> i) & 1u;
+        slot += head;
+        const int64_t gp = b0 + p;
+        a.perm[gp] = k | (head ? kHeadBit : 0u);
+        if (in_range(k, a.len, a.st)) a.irank[k] = (int32_t)slot;
+        if (head) {
+            if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)((sk & rmaskx) + row_lo);
+            const uint32_t lowcol = (uint32_t)(sk >> rbits);
+            if (in_range(lowcol, ncols, a.st)) atomicAdd(&s_col[lowcol], 1u);
+        }
+        if ((gp & tile_mask) == 0) a.tile_slot0[gp >> a.num_shift] = head ? slot : slot + 1;
+    }
+    __syncthreads();
+
+    // jcS of this bucket's columns: E + exclusive prefix of the unique counts.
+    {
+        constexpr int CPT_MAX = (1 << kMaxColBits) / THREADS;
+        const int cpt = ((1 << a.cs) + THREADS - 1) / THREADS;
+        uint32_t cnt[CPT_MAX];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int c = 0; c < CPT_MAX; ++c) {
+            const int col = tid * cpt + c;
+            cnt[c] = (c < cpt && col < ncols) ? s_col[col] : 0u;
+            sum += cnt[c];
+        }
+        uint32_t tot;
+        uint32_t run = E + block_exclusive_scan<THREADS>(sum, s_scan, &tot);
+#pragma unroll
+        for (int c = 0; c < CPT_MAX; ++c) {
+            const int col = tid * cpt + c;
+            if (c < cpt && col < ncols) a.jcS[col0 + col] = (int32_t)run;
+            run += cnt[c];
+        }
+        if (x == a.nb - 1 && tid == 0) {
+            a.jcS[a.n] = (int32_t)(E + U);
+            a.st->nnz = E + U;
+            a.tile_slot0[a.ntiles_num] = E + U;
+        }
+    }
+
+    // Fused numeric fold: every run from +0.0 in ascending k.
+    if (a.sr != nullptr) {
+        double val[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const int p = pbase + i;
+            val[i] = 0.0;
+            if (p < nx) {
+                const uint32_t k = (uint32_t)(s_w[p] & kmask);
+                val[i] = k < a.len ? __ldg(a.sr + k) : 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+            if (pbase + i < nx) s_val[pbase + i] = val[i];
+        __syncthreads();
+        for (uint32_t h = tid; h < U; h += THREADS) {
+            const int lo = s_hpos[h], hi = s_hpos[h + 1];
+            double acc = 0.0;
+            for (int p = lo; p < hi; ++p) acc += s_val[p];
+            const int64_t dst = (int64_t)E + h;
+            if (in_range(dst, a.len, a.st)) a.prS[dst] = acc;
+        }
+    }
+}
+
+template <int THREADS, int IPT>
+static fsparse_status run_emit(const BucketEmitArgs &a, int64_t nb, cudaStream_t s) {
+    using S = BucketSmem<THREADS, IPT>;
+    auto kern = bucket_emit_kernel<THREADS, IPT>;
+    FSP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes));
+    kern<<<(unsigned)nb, THREADS, S::bytes, s>>>(a);
+    FSP_LAUNCHED();
+    return FSPARSE_OK;
+}
+
+static int log2i(int x) {
+    int r = 0;
+    while ((1 << r) < x) ++r;
+    return r;
+}
+
+fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr, double *prS,
+                               int64_t len, int32_t m, int32_t n, const KeyLayout &key,
+                               const fsparse_config &cfg, Plan &plan, DevStatus *st, Scratch &scratch,
+                               cudaStream_t s) {
+    BucketShape sh;
+    if (!bucket_shape(len, n, key, cfg, &sh)) return set_error(FSPARSE_ERR_ARG, "bucket path does not fit");
+    const int nb = (int)sh.nb;
+    const size_t table = (size_t)nb * 4;
+    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (200u << 10) / std::max<size_t>(table, 1)));
+    int G = sm_count(0) * per_sm;
+    G = (int)std::max<int64_t>(1, std::min<int64_t>(G, (len + 4095) / 4096));
+    sh.grid = G;
+
+    uint32_t *hist, *goff, *tot, *bstart, *look, *ticket;
+    uint64_t *words;
+    fsparse_status e;
+    if ((e = scratch.get(&hist, (size_t)nb * G)) || (e = scratch.get(&goff, (size_t)nb * G)) ||
+        (e = scratch.get(&tot, (size_t)nb)) || (e = scratch.get(&bstart, (size_t)nb + 1)) ||
+        (e = scratch.get(&look, (size_t)nb + 1)) || (e = scratch.get(&ticket, 1)) ||
+        (e = scratch.get(&words, (size_t)len)))
+        return e;
+    FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)nb + 1) * 4, s));
+    FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
+
+    FSP_CUDA(cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
+    bucket_count_kernel<<<G, 1024, table, s>>>(jj, len, n, sh.cs, nb, hist, st);
+    FSP_LAUNCHED();
+    bucket_colprefix_kernel<<<(nb + 255) / 256, 256, 0, s>>>(hist, goff, tot, nb, G);
+    FSP_LAUNCHED();
+    if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
+    FSP_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
+    bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
+                                                 words, st);
+    FSP_LAUNCHED();
+
+    BucketEmitArgs a{};
+    a.words = words;
+    a.bstart = bstart;
+    a.nb = nb;
+    a.cs = sh.cs;
+    a.rb = key.rb;
+    a.kb = sh.kb;
+    a.n = n;
+    a.len = len;
+    a.sr = sr;
+    a.prS = prS;
+    a.perm = plan.perm;
+    a.irank = plan.irank;
+    a.irS = plan.irS;
+    a.jcS = plan.jcS;
+    a.tile_slot0 = plan.tile_slot0;
+    a.num_shift = log2i(plan.numeric_tile);
+    a.ntiles_num = plan.ntiles;
+    a.look = look;
+    a.ticket = ticket;
+    a.st = st;
+    if (sh.variant == 0) return run_emit<256, 16>(a, nb, s);
+    return run_emit<512, 16>(a, nb, s);
 }
 
 }  // namespace fsp

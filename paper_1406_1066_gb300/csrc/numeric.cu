@@ -3,13 +3,10 @@
 // Numeric fold (Eq. (2.3) with the App. A insert order): the plan stores the
 // sorted order perm[p] = k, with kHeadBit on the first triplet of every run
 // (one run per CCS slot), and tile_slot0[q] = number of runs that start
-// before numeric tile q.  A block takes a tile of NT positions, stages the
-// perm entries and the gathered values sr[k] in shared memory (plus a halo
-// for the run that crosses the tile end), lists the run heads in position
-// order with warp ballots, and lets ONE thread fold each run from +0.0 in
-// ascending position order -- which is ascending k, the paper's order --
-// so the result is identical to the serial insert, bit for bit, for any
-// launch shape.  No atomics touch values.
+// before numeric tile q.  ONE thread folds each run from +0.0 in ascending
+// position order -- which is ascending k, the paper's order -- so the result
+// is identical to the serial insert, bit for bit, for any launch shape.  No
+// atomics touch values.
 //
 // Adjoint: ds[k] = dprS[irank[k]], the transpose of the fold (the map is
 // linear in sr); 128-bit loads of irank and stores of ds.
@@ -27,139 +24,134 @@ __device__ __forceinline__ double gather(const double *__restrict__ sr, uint32_t
     return k < len ? __ldg(sr + k) : 0.0;
 }
 
-template <int NT, int THREADS>
-struct NumericSmem {
-    static constexpr int HALO = 64;
-    static constexpr int ROWS = NT / THREADS, WARPS = THREADS / 32;
-    static constexpr size_t bytes =
-        (size_t)(NT + HALO) * 8 + (size_t)(NT + HALO) * 4 + (size_t)NT * 2 + (ROWS * WARPS + 4) * 4;
-};
-
-template <int NT, int THREADS>
+// Register-blocked fold.  Thread t of a tile owns IPT consecutive positions:
+// it loads their perm entries with 128-bit loads, issues all IPT value
+// gathers at once, and folds every run that starts in its chunk in
+// registers.  A run that crosses the chunk end continues through the leading
+// segments (positions before the first run head) of the following threads,
+// which are published in shared memory column-major (conflict-free), and,
+// at the tile end, through a prefetched halo of the next tile.
+template <int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS)
     numeric_kernel(const uint32_t *__restrict__ perm, const double *__restrict__ sr,
                    const uint32_t *__restrict__ tile_slot0, double *__restrict__ prS, int64_t len,
                    int64_t ntiles, int64_t nnz) {
-    using S = NumericSmem<NT, THREADS>;
-    constexpr int HALO = S::HALO, ROWS = S::ROWS, WARPS = S::WARPS;
-    extern __shared__ __align__(16) unsigned char smem[];
-    double *s_val = reinterpret_cast<double *>(smem);
-    uint32_t *s_perm = reinterpret_cast<uint32_t *>(s_val + NT + HALO);
-    uint16_t *s_head = reinterpret_cast<uint16_t *>(s_perm + NT + HALO);
-    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_head + NT);   // [ROWS*WARPS] + nheads + halo_end
-    uint32_t *s_misc = s_cnt + ROWS * WARPS;
+    constexpr int NT = THREADS * IPT, HALO = 32;
+    __shared__ double s_lead[NT + HALO];     // [j * THREADS + t]: leading values of thread t
+    __shared__ uint8_t s_nlead[THREADS];     // leading-segment length of each thread
+    __shared__ uint8_t s_ends[THREADS];      // 1 if a run head lies in the thread's chunk
+    __shared__ uint32_t s_scan[THREADS / 32 + 1];
+    __shared__ int s_halo;                   // halo positions before the next head (HALO+1: none)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool vec = (reinterpret_cast<uintptr_t>(perm) & 15) == 0;
     for (int64_t q = blockIdx.x; q < ntiles; q += gridDim.x) {
         const int64_t P0 = q * NT;
         const int cnt = (int)min64(NT, len - P0);
-        const int ext = (int)min64(HALO, len - P0 - cnt);
-        if (cnt == NT && vec) {
-            for (int v = tid; v < NT / 4; v += THREADS)
-                reinterpret_cast<uint4 *>(s_perm)[v] = reinterpret_cast<const uint4 *>(perm + P0)[v];
+        const int first = tid * IPT;
+        const int nval = max(0, min(IPT, cnt - first));
+        uint32_t pm[IPT];
+        if (nval == IPT && vec) {
+#pragma unroll
+            for (int v = 0; v < IPT / 4; ++v) {
+                const uint4 x = reinterpret_cast<const uint4 *>(perm + P0 + first)[v];
+                pm[4 * v] = x.x;
+                pm[4 * v + 1] = x.y;
+                pm[4 * v + 2] = x.z;
+                pm[4 * v + 3] = x.w;
+            }
         } else {
-            for (int j = tid; j < cnt; j += THREADS) s_perm[j] = perm[P0 + j];
+#pragma unroll
+            for (int i = 0; i < IPT; ++i) pm[i] = i < nval ? perm[P0 + first + i] : kHeadBit;
         }
-        for (int j = tid; j < ext; j += THREADS) s_perm[cnt + j] = perm[P0 + cnt + j];
-        __syncthreads();
+        double v[IPT];
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) v[i] = i < nval ? gather(sr, pm[i], len) : 0.0;
+        uint32_t hmask = 0;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+            if (i < nval && (pm[i] & kHeadBit)) hmask |= 1u << i;
+        const int lead = hmask ? __ffs(hmask) - 1 : nval;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i)
+            if (i < lead) s_lead[i * THREADS + tid] = v[i];
+        s_nlead[tid] = (uint8_t)lead;
+        s_ends[tid] = hmask != 0 || nval < IPT;   // a short chunk is the end of the data
+        // The last warp prefetches the halo: where the tile's last run may go on.
+        if (warp == THREADS / 32 - 1) {
+            const int64_t hp = P0 + cnt + lane;
+            const bool in = cnt == NT && hp < len;
+            const uint32_t x = in ? perm[hp] : kHeadBit;
+            const uint32_t hm = __ballot_sync(0xffffffffu, x & kHeadBit);
+            const int end = hm ? __ffs(hm) - 1 : HALO + 1;   // HALO+1: the run goes past the halo
+            if (lane < (end > HALO ? HALO : end)) s_lead[NT + lane] = gather(sr, x, len);
+            if (lane == 0) s_halo = end;
+        }
+        uint32_t tile_heads;
+        const uint32_t excl = block_exclusive_scan<THREADS>(__popc(hmask), s_scan, &tile_heads);
 
-        // Gather the tile's values; warp 0 also finds where the halo's first run starts.
-#pragma unroll 4
-        for (int j = tid; j < cnt; j += THREADS) s_val[j] = gather(sr, s_perm[j], len);
-        if (warp == 0) {
-            int end = ext;
-            for (int b = 0; b < ext; b += 32) {
-                const bool h = b + lane < ext && (s_perm[cnt + b + lane] & kHeadBit);
-                const uint32_t m = __ballot_sync(0xffffffffu, h);
-                if (m) {
-                    end = b + __ffs(m) - 1;
-                    break;
-                }
+        // Runs that start in this chunk, folded in registers from +0.0.
+        int64_t slot = (int64_t)tile_slot0[q] + excl;
+        double acc = 0.0;
+        bool open = false;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            if ((hmask >> i) & 1u) {
+                if (open && slot < nnz) prS[slot] = acc;
+                slot += open;
+                acc = 0.0;   // +0.0: the insert adds into zeroed storage
+                open = true;
             }
-            if (lane == 0) s_misc[1] = (uint32_t)end;
+            if (open && i < nval) acc += v[i];
         }
-        // Run heads in position order: row r covers positions r*THREADS + tid.
-        uint32_t hm[ROWS];
-#pragma unroll
-        for (int r = 0; r < ROWS; ++r) {
-            const int j = r * THREADS + tid;
-            hm[r] = __ballot_sync(0xffffffffu, j < cnt && (s_perm[j] & kHeadBit));
-            if (lane == 0) s_cnt[r * WARPS + warp] = __popc(hm[r]);
-        }
-        __syncthreads();
-        const int halo_end = (int)s_misc[1];
-        for (int j = tid; j < halo_end; j += THREADS)
-            s_val[cnt + j] = gather(sr, s_perm[cnt + j], len);
-        if (warp == 0) {
-            uint32_t carry = 0;
-            for (int b = 0; b < ROWS * WARPS; b += 32) {
-                const uint32_t x = b + lane < ROWS * WARPS ? s_cnt[b + lane] : 0u;
-                uint32_t inc = x;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                if (b + lane < ROWS * WARPS) s_cnt[b + lane] = carry + inc - x;
-                carry += __shfl_sync(0xffffffffu, inc, 31);
+        if (open) {
+            // Continue through the leading segments of the following threads.
+            bool done = nval < IPT;
+            int t = tid + 1;
+            for (; !done && t < THREADS; ++t) {
+                const int nl = s_nlead[t];
+                for (int j = 0; j < nl; ++j) acc += s_lead[j * THREADS + t];
+                done = s_ends[t];
             }
-            if (lane == 0) s_misc[0] = carry;
-        }
-        __syncthreads();
+            if (!done) {
+                const int h = s_halo;
+                const int take = h > HALO ? HALO : h;
+                for (int j = 0; j < take; ++j) acc += s_lead[NT + j];
+                if (h > HALO) {
+                    // Longer than the halo: stream the rest, eight at a time, in order.
+                    int64_t g = P0 + cnt + HALO;
+                    while (g < len) {
+                        uint32_t x[8];
+                        int c = 0;
 #pragma unroll
-        for (int r = 0; r < ROWS; ++r)
-            if ((hm[r] >> lane) & 1u)
-                s_head[s_cnt[r * WARPS + warp] + __popc(hm[r] & lanemask_lt())] =
-                    (uint16_t)(r * THREADS + tid);
-        __syncthreads();
-
-        const int nh = (int)s_misc[0];
-        const int64_t base = tile_slot0[q];
-        for (int h = tid; h < nh; h += THREADS) {
-            const int start = s_head[h];
-            const bool last = h + 1 == nh;
-            const int end = last ? cnt + halo_end : s_head[h + 1];
-            double acc = 0.0;   // +0.0: the insert adds into zeroed storage
-            for (int p = start; p < end; ++p) acc += s_val[p];
-            if (last && halo_end == ext) {
-                // A run longer than the halo: continue through global memory,
-                // eight triplets at a time, still in ascending order.
-                int64_t g = P0 + cnt + ext;
-                while (g < len) {
-                    uint32_t x[8];
-                    int c = 0;
+                        for (int u = 0; u < 8; ++u) x[u] = g + u < len ? perm[g + u] : kHeadBit;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) x[u] = g + u < len ? perm[g + u] : kHeadBit;
+                        for (int u = 0; u < 8; ++u)
+                            if (c == u && !(x[u] & kHeadBit)) ++c;
+                        double w[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (c == u && !(x[u] & kHeadBit)) ++c;
+                        for (int u = 0; u < 8; ++u) w[u] = u < c ? gather(sr, x[u], len) : 0.0;
+                        for (int u = 0; u < c; ++u) acc += w[u];
+                        if (c < 8) break;
+                        g += 8;
                     }
-                    double v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = u < c ? gather(sr, x[u], len) : 0.0;
-                    for (int u = 0; u < c; ++u) acc += v[u];
-                    if (c < 8) break;
-                    g += 8;
                 }
             }
-            if (base + h < nnz) prS[base + h] = acc;
+            if (slot < nnz) prS[slot] = acc;
         }
-        __syncthreads();
+        __syncthreads();   // s_lead / s_nlead are reused by the next tile
     }
 }
 
-template <int NT, int THREADS>
+template <int THREADS, int IPT>
 static fsparse_status run_numeric(const uint32_t *perm, const uint32_t *tile_slot0, int64_t len,
                                   int64_t ntiles, const double *sr, double *prS, int64_t nnz,
                                   cudaStream_t s) {
-    using S = NumericSmem<NT, THREADS>;
-    auto kern = numeric_kernel<NT, THREADS>;
-    FSP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes));
+    auto kern = numeric_kernel<THREADS, IPT>;
     int per_sm = 0;
-    FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, S::bytes));
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(0) * std::max(per_sm, 1));
-    kern<<<(unsigned)grid, THREADS, S::bytes, s>>>(perm, sr, tile_slot0, prS, len, ntiles, nnz);
+    FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0));
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(0) * std::max(per_sm, 1) * 8);
+    kern<<<(unsigned)grid, THREADS, 0, s>>>(perm, sr, tile_slot0, prS, len, ntiles, nnz);
     FSP_LAUNCHED();
     return FSPARSE_OK;
 }
@@ -172,9 +164,9 @@ fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *tile_slot0, 
     // the fold is fused into the symbolic call; then the caller passes cap = len).
     const int64_t nnz_bound = cap > 0 ? cap : len;
     if (len > 0) {
-        if (tile == 1024) e = run_numeric<1024, 256>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
-        else if (tile == 2048) e = run_numeric<2048, 256>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
-        else if (tile == 4096) e = run_numeric<4096, 256>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
+        if (tile == 1024) e = run_numeric<128, 8>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
+        else if (tile == 2048) e = run_numeric<128, 16>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
+        else if (tile == 4096) e = run_numeric<256, 16>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
         else return set_error(FSPARSE_ERR_ARG, "unsupported numeric tile");
         if (e != FSPARSE_OK) return e;
     }

@@ -9,7 +9,7 @@
 //
 //   1. one read of ii/jj counts every digit of every pass at once;
 //   2. one kernel per digit: each block takes a tile by atomic ticket,
-//      ranks its items per digit inside every warp with ballots, publishes
+//      ranks its items per digit inside every warp (rank.cuh), publishes
 //      its digit counts, resolves its global offsets by decoupled
 //      look-back over earlier tiles, and writes the tile out through shared
 //      memory so that each digit's run is stored contiguously;
@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "internal.hpp"
+#include "rank.cuh"
 
 namespace fsp {
 
@@ -123,7 +124,7 @@ struct PassArgs {
 template <int R, int THREADS, int ITEMS>
 struct PassSmem {
     static constexpr int RADIX = 1 << R, WARPS = THREADS / 32, TILE = THREADS * ITEMS;
-    static constexpr size_t bytes = TILE * 8 + TILE * 4 + WARPS * RADIX * 4 + RADIX * 4 * 3 +
+    static constexpr size_t bytes = TILE * 8 + TILE * 4 + 2 * WARPS * RADIX * 4 + RADIX * 4 * 3 +
                                     (THREADS / 32 + 2) * 4 + 16;
 };
 
@@ -136,7 +137,8 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
     uint64_t *s_keys = reinterpret_cast<uint64_t *>(smem);
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
     uint32_t *s_wcnt = s_vals + TILE;                 // [WARPS][RADIX]
-    uint32_t *s_local = s_wcnt + WARPS * RADIX;       // [RADIX] tile-local digit start
+    uint32_t *s_wm = s_wcnt + WARPS * RADIX;          // [WARPS][RADIX] peer masks
+    uint32_t *s_local = s_wm + WARPS * RADIX;         // [RADIX] tile-local digit start
     uint32_t *s_global = s_local + RADIX;             // [RADIX] global digit start of this tile
     uint32_t *s_total = s_global + RADIX;             // [RADIX]
     uint32_t *s_scan = s_total + RADIX;               // block scan scratch
@@ -144,7 +146,10 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) *s_tile = atomicAdd(a.ticket, 1u);
-    for (int t = tid; t < WARPS * RADIX; t += THREADS) s_wcnt[t] = 0;
+    for (int t = tid; t < WARPS * RADIX; t += THREADS) {
+        s_wcnt[t] = 0;
+        s_wm[t] = 0;
+    }
     __syncthreads();
     const int64_t tile = *s_tile;
     const int64_t base = tile * TILE;
@@ -174,26 +179,15 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
         }
     }
 
-    // Warp-level ranking with ballots: peers = lanes holding the same digit.
-    uint32_t *wc = s_wcnt + warp * RADIX;
+    // Warp-level stable ranking: peers = lanes holding the same digit.
+    uint32_t dig[ITEMS];
+    bool valid[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        const bool valid = wbase + i * 32 < a.len;
-        const uint32_t d = (uint32_t)(key[i] & MASK);
-        uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-        for (int b = 0; b < R; ++b) {
-            const uint32_t bit = (d >> b) & 1u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bal : ~bal;
-        }
-        uint32_t before = 0;
-        if (valid) before = wc[d];
-        __syncwarp();
-        if (valid && lane == 31 - __clz(peers)) wc[d] = before + __popc(peers);
-        __syncwarp();
-        rnk[i] = before + __popc(peers & lanemask_lt());
+        valid[i] = wbase + i * 32 < a.len;
+        dig[i] = (uint32_t)(key[i] & MASK);
     }
+    warp_rank<R, ITEMS>(dig, valid, s_wcnt + warp * RADIX, s_wm + warp * RADIX, rnk);
     __syncthreads();
 
     // Per digit: exclusive offsets across warps, tile total.

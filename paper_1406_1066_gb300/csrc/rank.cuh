@@ -1,12 +1,14 @@
-// rank.cuh -- stable block-local ranking of radix digits (warp ballots).
+// rank.cuh -- stable block-local ranking of radix digits.
 //
 // Items are held warp-striped: item i of lane l in warp w sits at block
 // position w*32*ITEMS + i*32 + l, so visiting (warp, i, lane) in order
 // visits positions in order.  For every item the warp finds its peers (the
-// lanes holding the same digit) with one ballot per digit bit, ranks the
+// lanes holding the same digit), ranks the
 // item among its earlier peers, and keeps a running count per (warp, digit)
 // in shared memory.  A block-wide pass then turns the counts into exclusive
 // offsets ordered by (digit, warp), which makes the whole ranking stable.
+// (Finding peers with warp ballots takes one ballot per digit bit; a shared
+// atomicOr per item measured about four times faster on GB300.)
 #pragma once
 
 #include "common.cuh"
@@ -14,27 +16,32 @@
 namespace fsp {
 
 // Rank ITEMS digits per thread inside the warp.  `wc` points at this warp's
-// RADIX counters (zeroed).  rnk[i] receives the rank among earlier items of
-// the same digit in this warp.
+// RADIX counters and `wm` at its RADIX peer masks (both zeroed).  rnk[i]
+// receives the rank among earlier items of the same digit in this warp.
+// Peers are found by OR-ing each lane's bit into the mask of its digit in
+// shared memory and reading the mask back (one atomic and one load per item,
+// instead of one ballot per digit bit); the highest peer then advances the
+// counter and clears the mask for the next item.
 template <int R, int ITEMS>
 __device__ __forceinline__ void warp_rank(const uint32_t (&digit)[ITEMS], const bool (&valid)[ITEMS],
-                                          uint32_t *wc, uint32_t (&rnk)[ITEMS]) {
+                                          uint32_t *wc, uint32_t *wm, uint32_t (&rnk)[ITEMS]) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const uint32_t d = digit[i];
-        uint32_t peers = __ballot_sync(0xffffffffu, valid[i]);
-#pragma unroll
-        for (int b = 0; b < R; ++b) {
-            const uint32_t bit = (d >> b) & 1u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bal : ~bal;
-        }
-        uint32_t before = 0;
-        if (valid[i]) before = wc[d];
+        if (valid[i]) atomicOr(&wm[d], 1u << lane);
         __syncwarp();
-        if (valid[i] && lane == 31 - __clz(peers)) wc[d] = before + __popc(peers);
+        uint32_t peers = 0, before = 0;
+        if (valid[i]) {
+            peers = wm[d];
+            before = wc[d];
+        }
+        __syncwarp();
+        if (valid[i] && lane == 31 - __clz(peers)) {
+            wc[d] = before + __popc(peers);
+            wm[d] = 0;
+        }
         __syncwarp();
         rnk[i] = before + __popc(peers & lt);
     }
