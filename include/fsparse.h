@@ -217,6 +217,40 @@ fsparse_status fsparse_tune_load(const char *path);
 fsparse_status fsparse_tune_clear(void);
 
 /* ------------------------------------------------------------------------
+ * Assembly without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that are not allowed to allocate GPU
+ * memory themselves or through this library -- code running under another
+ * framework's memory manager or arena, solver loops that forbid allocation
+ * after start-up, plug-ins that only receive pre-allocated buffers.
+ *
+ * Same result as fsparse_assemble (bit for bit) for problems within the
+ * limits below, written to caller-owned device buffers: irank int32[len],
+ * jcS int32[n+1], irS int32[len], prS double[len] (the first *nnz_out
+ * entries of irS/prS are the CCS arrays).  m and n must be given (> 0);
+ * there is no nzmax and no plan.  *nnz_out is a HOST int64.
+ *
+ * Working memory: one static device array of FSPARSE_NOALLOC_SCRATCH_BYTES
+ * inside this library, which every GPU that loads the library keeps until
+ * the process exits.  The entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (other streams or threads, without ordering) race and must not be
+ * issued.  Synchronises `stream` once to read nnz.
+ *
+ * len > FSPARSE_NOALLOC_MAX_LEN or n > FSPARSE_NOALLOC_MAX_COLS returns
+ * FSPARSE_ERR_SIZE before touching the device.
+ * ---------------------------------------------------------------------- */
+#define FSPARSE_NOALLOC_MAX_LEN 131072
+#define FSPARSE_NOALLOC_MAX_COLS 131072
+#define FSPARSE_NOALLOC_SCRATCH_BYTES (5u << 20)
+
+fsparse_status fsparse_assemble_noalloc(const int32_t *ii, const int32_t *jj, const double *sr,
+                                        int64_t len, int32_t m, int32_t n, int32_t *irank,
+                                        int32_t *jcS, int32_t *irS, double *prS,
+                                        int64_t *nnz_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Diagnostics.
  * ---------------------------------------------------------------------- */
 /* Human-readable text of the last error raised on the calling thread. */

@@ -85,6 +85,16 @@ Scratch::~Scratch() {
 }
 
 fsparse_status Scratch::alloc(void **p, size_t bytes) {
+    if (arena_) {
+        const size_t take = (std::max<size_t>(bytes, 16) + 255) & ~size_t(255);
+        if (arena_used_ + take > arena_bytes_) {
+            *p = nullptr;
+            return set_error(FSPARSE_ERR_SIZE, "static scratch exhausted");
+        }
+        *p = arena_ + arena_used_;
+        arena_used_ += take;
+        return FSPARSE_OK;
+    }
     if (n_ == 32) return set_error(FSPARSE_ERR_NOMEM, "too many scratch buffers");
     fsparse_status e = device_alloc(p, bytes, s_);
     if (e == FSPARSE_OK) ptrs_[n_++] = *p;

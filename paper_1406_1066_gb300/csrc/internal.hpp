@@ -91,6 +91,9 @@ fsparse_config default_config(int64_t len, const KeyLayout &key);
 class Scratch {
   public:
     explicit Scratch(cudaStream_t s) : s_(s) {}
+    // Bump allocation from caller-provided device memory instead of the pool
+    // (nothing is allocated or freed; used by fsparse_assemble_noalloc).
+    Scratch(cudaStream_t s, void *arena, size_t bytes) : s_(s), arena_(static_cast<char *>(arena)), arena_bytes_(bytes) {}
     ~Scratch();
     fsparse_status alloc(void **p, size_t bytes);
     template <class T>
@@ -102,6 +105,8 @@ class Scratch {
     cudaStream_t s_;
     void *ptrs_[32] = {};
     int n_ = 0;
+    char *arena_ = nullptr;
+    size_t arena_bytes_ = 0, arena_used_ = 0;
 };
 
 fsparse_status device_alloc(void **p, size_t bytes, cudaStream_t s);

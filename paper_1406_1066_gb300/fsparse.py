@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
         "fsparse_tune_save": [ctypes.c_char_p],
         "fsparse_tune_load": [ctypes.c_char_p],
         "fsparse_tune_clear": [],
+        "fsparse_assemble_noalloc": [_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P,
+                                     ctypes.POINTER(_I64), _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
