@@ -135,10 +135,10 @@ static void release_device(void *const *ptrs, int count) {
 }
 
 static void free_plan_arrays(Plan &p) {
-    void *ptrs[5] = {p.irank, p.jcS, p.irS, p.perm, p.tile_slot0};
+    void *ptrs[5] = {p.irank, p.jcS, p.irS, p.perm, p.chunk_slot0};
     release_device(ptrs, 5);
     p.irank = p.jcS = p.irS = nullptr;
-    p.perm = p.tile_slot0 = nullptr;
+    p.perm = p.chunk_slot0 = nullptr;
 }
 
 constexpr int64_t kMaxLen = kMaxLookbackValue;   // 2^30 - 1
@@ -170,8 +170,7 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     if ((e = emit_from_perm(ii, jj, len, plan.m, plan.n, plan.key, plan, d_st, scratch, s)) != FSPARSE_OK)
         return e;
     if (sr) {
-        e = launch_numeric(plan.perm, plan.tile_slot0, len, plan.ntiles, plan.numeric_tile, sr, prS,
-                           0, 0, s);
+        e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s);
         if (e == FSPARSE_OK) *folded = true;
     }
     return e;
@@ -213,7 +212,7 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     fsparse_config cfg = force ? *force : resolve_config(len, plan->key);
     plan->cfg = cfg;
     plan->numeric_tile = cfg.numeric_tile;
-    plan->ntiles = (len + cfg.numeric_tile - 1) / cfg.numeric_tile;
+    plan->nchunks = (len + kChunk - 1) / kChunk;
     const int64_t irs_cap = std::max<int64_t>(std::max<int64_t>(len, nzmax), 1);
 
     auto fail = [&](fsparse_status st) {
@@ -225,13 +224,13 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
         (e = device_alloc(reinterpret_cast<void **>(&plan->perm), (size_t)std::max<int64_t>(len, 1) * 4, s)) ||
         (e = device_alloc(reinterpret_cast<void **>(&plan->irS), (size_t)irs_cap * 4, s)) ||
         (e = device_alloc(reinterpret_cast<void **>(&plan->jcS), ((size_t)n + 1) * 4, s)) ||
-        (e = device_alloc(reinterpret_cast<void **>(&plan->tile_slot0), ((size_t)plan->ntiles + 1) * 4, s)))
+        (e = device_alloc(reinterpret_cast<void **>(&plan->chunk_slot0), ((size_t)plan->nchunks + 1) * 4, s)))
         return fail(e);
 
     bool folded = false;
     if (len == 0) {
         if (cudaMemsetAsync(plan->jcS, 0, ((size_t)n + 1) * 4, s) != cudaSuccess ||
-            cudaMemsetAsync(plan->tile_slot0, 0, 4, s) != cudaSuccess)
+            cudaMemsetAsync(plan->chunk_slot0, 0, 4, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
         folded = sr != nullptr;
     } else {
@@ -321,7 +320,7 @@ fsparse_status fsparse_numeric(fsparse_plan plan, const double *sr, double *prS,
     if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
     const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
     if ((p.len > 0 && !sr) || (p.cap > 0 && !prS)) return set_error(FSPARSE_ERR_ARG, "NULL array");
-    return launch_numeric(p.perm, p.tile_slot0, p.len, p.ntiles, p.numeric_tile, sr, prS, p.nnz, p.cap,
+    return launch_numeric(p.perm, p.chunk_slot0, p.len, p.numeric_tile, sr, prS, p.nnz, p.cap,
                           as_stream(stream));
 }
 
@@ -352,8 +351,7 @@ fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const doub
     if (e != FSPARSE_OK) return e;
     *plan_out = reinterpret_cast<fsparse_plan>(p);
     if (prS_capacity < p->cap) return set_error(FSPARSE_ERR_NZMAX, "prS capacity below the plan's cap");
-    return launch_numeric(p->perm, p->tile_slot0, p->len, p->ntiles, p->numeric_tile, sr, prS, p->nnz,
-                          p->cap, s);
+    return launch_numeric(p->perm, p->chunk_slot0, p->len, p->numeric_tile, sr, prS, p->nnz, p->cap, s);
 }
 
 // ---- batch ----------------------------------------------------------------
@@ -380,9 +378,9 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
     bt->h_len_off = new (std::nothrow) int64_t[count + 1];
     bt->h_nnz_off = new (std::nothrow) int64_t[count + 1];
     bt->numeric_tile = 4096;
-    bt->ntiles = (total_len + bt->numeric_tile - 1) / bt->numeric_tile;
+    bt->nchunks = (total_len + kChunk - 1) / kChunk;
     auto fail = [&](fsparse_status st) {
-        void *ptrs[2] = {bt->perm, bt->tile_slot0};
+        void *ptrs[2] = {bt->perm, bt->chunk_slot0};
         release_device(ptrs, 2);
         delete[] bt->h_len_off;
         delete[] bt->h_nnz_off;
@@ -392,7 +390,7 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
     if (!bt->h_len_off || !bt->h_nnz_off) return fail(set_error(FSPARSE_ERR_NOMEM, "host allocation"));
     fsparse_status e;
     if ((e = device_alloc(reinterpret_cast<void **>(&bt->perm), (size_t)std::max<int64_t>(total_len, 1) * 4, s)) ||
-        (e = device_alloc(reinterpret_cast<void **>(&bt->tile_slot0), ((size_t)bt->ntiles + 1) * 4, s)))
+        (e = device_alloc(reinterpret_cast<void **>(&bt->chunk_slot0), ((size_t)bt->nchunks + 1) * 4, s)))
         return fail(e);
     int64_t lo = 0, no = 0;
     for (int32_t b = 0; b < count; ++b) {
@@ -410,13 +408,13 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
         uint32_t *counts = nullptr;
         DevStatus *d_st = nullptr;
         DevStatus h_st{};
-        if ((e = scratch.get(&counts, (size_t)bt->ntiles + 1)) != FSPARSE_OK) return fail(e);
+        if ((e = scratch.get(&counts, (size_t)bt->nchunks + 1)) != FSPARSE_OK) return fail(e);
         if ((e = scratch.get(&d_st, 1)) != FSPARSE_OK) return fail(e);
         if (cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
-        if ((e = launch_tile_heads(bt->perm, total_len, bt->numeric_tile, counts, bt->ntiles, s)) != FSPARSE_OK)
+        if ((e = launch_chunk_heads(bt->perm, total_len, counts, bt->nchunks, s)) != FSPARSE_OK)
             return fail(e);
-        if ((e = exclusive_scan_u32(counts, bt->tile_slot0, bt->ntiles, d_st, scratch, s)) != FSPARSE_OK)
+        if ((e = exclusive_scan_u32(counts, bt->chunk_slot0, bt->nchunks, d_st, scratch, s)) != FSPARSE_OK)
             return fail(e);
         if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
         if (h_st.timeout) return fail(set_error(FSPARSE_ERR_TIMEOUT, "device look-back wait expired"));
@@ -440,8 +438,8 @@ fsparse_status fsparse_batch_numeric(fsparse_batch batch, const double *sr_conca
     if (!batch) return set_error(FSPARSE_ERR_ARG, "batch is NULL");
     const Batch &b = reinterpret_cast<fsparse_batch_s *>(batch)->b;
     if (b.total_len > 0 && (!sr_concat || !prS_concat)) return set_error(FSPARSE_ERR_ARG, "NULL array");
-    return launch_numeric(b.perm, b.tile_slot0, b.total_len, b.ntiles, b.numeric_tile, sr_concat,
-                          prS_concat, b.total_nnz, b.total_nnz, as_stream(stream));
+    return launch_numeric(b.perm, b.chunk_slot0, b.total_len, b.numeric_tile, sr_concat, prS_concat,
+                          b.total_nnz, b.total_nnz, as_stream(stream));
 }
 
 fsparse_status fsparse_batch_destroy(fsparse_batch batch) {
@@ -450,7 +448,7 @@ fsparse_status fsparse_batch_destroy(fsparse_batch batch) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != b->device) cudaSetDevice(b->device);
-    void *ptrs[2] = {b->perm, b->tile_slot0};
+    void *ptrs[2] = {b->perm, b->chunk_slot0};
     release_device(ptrs, 2);
     if (cur != b->device) cudaSetDevice(cur);
     delete[] b->h_len_off;

@@ -22,7 +22,7 @@
 //                neighbours (the collision detection of Part 3), numbers the
 //                slots with one decoupled look-back across buckets, and writes
 //                perm, irank, irS, jcS (Part 4's prefix, per bucket column),
-//                the numeric tile bases and -- in a full assembly -- prS by
+//                the numeric chunk slot bases and -- in a full assembly -- prS by
 //                folding each run from +0.0 in ascending k.
 //
 // A bucket above the kernel's capacity, or a run longer than kRunSortMax,
@@ -139,9 +139,8 @@ struct BucketEmitArgs {
     double *prS;
     uint32_t *perm;
     int32_t *irank, *irS, *jcS;
-    uint32_t *tile_slot0;
-    int num_shift;
-    int64_t ntiles_num;
+    uint32_t *chunk_slot0;
+    int64_t nchunks;
     uint32_t *look;
     uint32_t *ticket;
     DevStatus *st;
@@ -150,14 +149,16 @@ struct BucketEmitArgs {
 template <int THREADS, int IPT>
 struct BucketSmem {
     static constexpr int CAP = THREADS * IPT, WARPS = THREADS / 32;
-    static constexpr size_t off_wcnt = (size_t)CAP * 8;
-    static constexpr size_t off_wm = off_wcnt + (size_t)WARPS * 256 * 4;
-    static constexpr size_t off_col = off_wm + (size_t)WARPS * 256 * 4;
-    static constexpr size_t off_local = off_col + (size_t)(1 << kMaxColBits) * 4;
+    // Region A: rank counters during the sort, then run head positions.
+    static constexpr size_t bytes_a = std::max<size_t>((size_t)WARPS * 256 * 4, ((size_t)(CAP + 1) * 2 + 15) / 16 * 16);
+    // Region B: peer masks during the sort, then per-column unique counts.
+    static constexpr size_t bytes_b = std::max<size_t>((size_t)WARPS * 256 * 4, (size_t)(1 << kMaxColBits) * 4);
+    static constexpr size_t off_a = (size_t)CAP * 8;
+    static constexpr size_t off_b = off_a + bytes_a;
+    static constexpr size_t off_local = off_b + bytes_b;
     static constexpr size_t off_scan = off_local + 256 * 4;
     static constexpr size_t off_misc = off_scan + (WARPS + 2) * 4;
-    static constexpr size_t off_hpos = off_misc + 16 * 4;
-    static constexpr size_t bytes = off_hpos + ((size_t)(CAP + 1) * 2 + 15) / 16 * 16;
+    static constexpr size_t bytes = off_misc + 16 * 4;
 };
 
 __device__ __forceinline__ int bits_of(uint32_t v) { return v ? 32 - __clz(v) : 0; }
@@ -168,14 +169,13 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
     constexpr int CAP = S::CAP, WARPS = S::WARPS;
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_w = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_wcnt = reinterpret_cast<uint32_t *>(smem + S::off_wcnt);
-    uint32_t *s_wm = reinterpret_cast<uint32_t *>(smem + S::off_wm);
-    uint32_t *s_col = reinterpret_cast<uint32_t *>(smem + S::off_col);
+    uint32_t *s_wcnt = reinterpret_cast<uint32_t *>(smem + S::off_a);    // sort
+    uint16_t *s_hpos = reinterpret_cast<uint16_t *>(smem + S::off_a);    // after the sort
+    uint32_t *s_wm = reinterpret_cast<uint32_t *>(smem + S::off_b);      // sort
+    uint32_t *s_col = reinterpret_cast<uint32_t *>(smem + S::off_b);     // after the sort
     uint32_t *s_local = reinterpret_cast<uint32_t *>(smem + S::off_local);
     uint32_t *s_scan = reinterpret_cast<uint32_t *>(smem + S::off_scan);
     uint32_t *s_misc = reinterpret_cast<uint32_t *>(smem + S::off_misc);
-    uint16_t *s_hpos = reinterpret_cast<uint16_t *>(smem + S::off_hpos);
-    double *s_val = reinterpret_cast<double *>(smem);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -279,25 +279,44 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
         __syncthreads();
     }
 
-    // Runs: a new run starts where the sort key changes (blocked positions).
-    const int pbase = tid * IPT;
-    uint32_t hmask = 0;
+    // Runs: a new run starts where the sort key changes.  Positions are read
+    // warp-striped (consecutive lanes, conflict-free); hb[i] holds the head
+    // flags of row i, so heads are counted in position order.
+    uint32_t hb[IPT];
+    uint32_t wheads = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-        const int p = pbase + i;
-        if (p < nx) {
-            const uint64_t sk = s_w[p] >> kb;
-            if (p == 0 || sk != (s_w[p - 1] >> kb)) hmask |= 1u << i;
-        }
+        const int p = warp * 32 * IPT + i * 32 + lane;
+        bool head = false;
+        if (p < nx) head = p == 0 || (s_w[p] >> kb) != (s_w[p - 1] >> kb);
+        hb[i] = __ballot_sync(0xffffffffu, head);
+        wheads += __popc(hb[i]);
     }
-    uint32_t U;
-    const uint32_t hexcl = block_exclusive_scan<THREADS>(__popc(hmask), s_scan, &U);
+    if (lane == 0) s_scan[warp] = wheads;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t c = lane < WARPS ? s_scan[lane] : 0u;
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < WARPS) s_scan[lane] = inc - c;
+        if (lane == WARPS - 1) s_scan[WARPS] = inc;
+    }
+    __syncthreads();
+    const uint32_t U = s_scan[WARPS];
+    const uint32_t wbase = s_scan[warp];
     if (tid == 0) st_release(a.look + x, (x == 0 ? kFlagInc : kFlagAgg) | U);
     {
-        uint32_t h = hexcl;
+        uint32_t run = wbase;
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
-        for (int i = 0; i < IPT; ++i)
-            if ((hmask >> i) & 1u) s_hpos[h++] = (uint16_t)(pbase + i);
+        for (int i = 0; i < IPT; ++i) {
+            if ((hb[i] >> lane) & 1u) s_hpos[run + __popc(hb[i] & lt)] = (uint16_t)(warp * 32 * IPT + i * 32 + lane);
+            run += __popc(hb[i]);
+        }
     }
     if (tid == 0) s_hpos[U] = (uint16_t)nx;
     for (int c = tid; c < (1 << a.cs); c += THREADS) s_col[c] = 0;
@@ -331,28 +350,57 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
     __syncthreads();
     const uint32_t E = s_misc[3];
 
-    // perm, irank, irS, column counts, numeric tile bases.
+    // perm, irank, irS, column counts, chunk slot bases (warp-striped).
     const uint64_t rmaskx = (1ull << rbits) - 1;
-    const uint32_t tile_mask = (1u << a.num_shift) - 1;
-    uint32_t slot = E + hexcl - 1;
+    {
+        uint32_t before = wbase;   // heads at earlier positions
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int p = pbase + i;
-        if (p >= nx) continue;
-        const uint64_t v = s_w[p];
-        const uint32_t k = (uint32_t)(v & kmask);
-        const uint64_t sk = v >> kb;
-        const bool head = (hmask >> i) & 1u;
-        slot += head;
-        const int64_t gp = b0 + p;
-        a.perm[gp] = k | (head ? kHeadBit : 0u);
-        if (in_range(k, a.len, a.st)) a.irank[k] = (int32_t)slot;
-        if (head) {
-            if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)((sk & rmaskx) + row_lo);
-            const uint32_t lowcol = (uint32_t)(sk >> rbits);
-            if (in_range(lowcol, ncols, a.st)) atomicAdd(&s_col[lowcol], 1u);
+        for (int i = 0; i < IPT; ++i) {
+            const int p = warp * 32 * IPT + i * 32 + lane;
+            const bool head = (hb[i] >> lane) & 1u;
+            const uint32_t slot = E + before + __popc(hb[i] & lt) + (head ? 0u : 0xffffffffu);
+            before += __popc(hb[i]);
+            if (p >= nx) continue;
+            const uint64_t v = s_w[p];
+            const uint32_t k = (uint32_t)(v & kmask);
+            const uint64_t sk = v >> kb;
+            const int64_t gp = b0 + p;
+            a.perm[gp] = k | (head ? kHeadBit : 0u);
+            if (in_range(k, a.len, a.st)) a.irank[k] = (int32_t)slot;
+            if (head) {
+                if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)((sk & rmaskx) + row_lo);
+                const uint32_t lowcol = (uint32_t)(sk >> rbits);
+                if (in_range(lowcol, ncols, a.st)) atomicAdd(&s_col[lowcol], 1u);
+            }
+            if ((gp & (kChunk - 1)) == 0) a.chunk_slot0[gp >> kChunkShift] = head ? slot : slot + 1;
         }
-        if ((gp & tile_mask) == 0) a.tile_slot0[gp >> a.num_shift] = head ? slot : slot + 1;
+    }
+
+    // Fused numeric fold: every run from +0.0 in ascending k, gathering the
+    // values straight from sr (eight independent loads at a time).
+    if (a.sr != nullptr) {
+        for (uint32_t h = tid; h < U; h += THREADS) {
+            const int lo = s_hpos[h], hi = s_hpos[h + 1];
+            double acc = 0.0;   // +0.0: the insert adds into zeroed storage
+            for (int p = lo; p < hi; p += 8) {
+                const int c = min(8, hi - p);
+                double w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    w[u] = 0.0;
+                    if (u < c) {
+                        const uint32_t k = (uint32_t)(s_w[p + u] & kmask);
+                        w[u] = k < a.len ? __ldg(a.sr + k) : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (u < c) acc += w[u];
+            }
+            const int64_t dst = (int64_t)E + h;
+            if (in_range(dst, a.len, a.st)) a.prS[dst] = acc;
+        }
     }
     __syncthreads();
 
@@ -379,33 +427,7 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
         if (x == a.nb - 1 && tid == 0) {
             a.jcS[a.n] = (int32_t)(E + U);
             a.st->nnz = E + U;
-            a.tile_slot0[a.ntiles_num] = E + U;
-        }
-    }
-
-    // Fused numeric fold: every run from +0.0 in ascending k.
-    if (a.sr != nullptr) {
-        double val[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-            const int p = pbase + i;
-            val[i] = 0.0;
-            if (p < nx) {
-                const uint32_t k = (uint32_t)(s_w[p] & kmask);
-                val[i] = k < a.len ? __ldg(a.sr + k) : 0.0;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < IPT; ++i)
-            if (pbase + i < nx) s_val[pbase + i] = val[i];
-        __syncthreads();
-        for (uint32_t h = tid; h < U; h += THREADS) {
-            const int lo = s_hpos[h], hi = s_hpos[h + 1];
-            double acc = 0.0;
-            for (int p = lo; p < hi; ++p) acc += s_val[p];
-            const int64_t dst = (int64_t)E + h;
-            if (in_range(dst, a.len, a.st)) a.prS[dst] = acc;
+            a.chunk_slot0[a.nchunks] = E + U;
         }
     }
 }
@@ -418,12 +440,6 @@ static fsparse_status run_emit(const BucketEmitArgs &a, int64_t nb, cudaStream_t
     kern<<<(unsigned)nb, THREADS, S::bytes, s>>>(a);
     FSP_LAUNCHED();
     return FSPARSE_OK;
-}
-
-static int log2i(int x) {
-    int r = 0;
-    while ((1 << r) < x) ++r;
-    return r;
 }
 
 fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr, double *prS,
@@ -476,9 +492,8 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const doubl
     a.irank = plan.irank;
     a.irS = plan.irS;
     a.jcS = plan.jcS;
-    a.tile_slot0 = plan.tile_slot0;
-    a.num_shift = log2i(plan.numeric_tile);
-    a.ntiles_num = plan.ntiles;
+    a.chunk_slot0 = plan.chunk_slot0;
+    a.nchunks = plan.nchunks;
     a.look = look;
     a.ticket = ticket;
     a.st = st;

@@ -17,6 +17,10 @@ namespace fsp {
 
 constexpr uint32_t kHeadBit = 0x80000000u;   // perm[p] | kHeadBit marks the first triplet of a run
 constexpr uint32_t kIndexMask = 0x7fffffffu;
+// The numeric fold works on chunks of kChunk sorted positions; the plan keeps
+// one slot base per chunk.
+constexpr int kChunk = 16;
+constexpr int kChunkShift = 4;
 
 // Look-back word layout: [31:30] flag, [29:0] value.
 constexpr uint32_t kFlagAgg = 1u << 30;      // tile aggregate only

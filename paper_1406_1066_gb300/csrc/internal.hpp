@@ -42,9 +42,9 @@ struct Plan {
     int32_t *jcS = nullptr;          // [n+1]
     int32_t *irS = nullptr;          // [max(len, nzmax, 1)]
     uint32_t *perm = nullptr;        // [len] sorted position -> k, kHeadBit on run heads
-    uint32_t *tile_slot0 = nullptr;  // [ntiles+1] slots before each numeric tile
-    int numeric_tile = 4096;
-    int64_t ntiles = 0;
+    uint32_t *chunk_slot0 = nullptr; // [nchunks+1] runs that start before each kChunk positions
+    int numeric_tile = 4096;         // positions per numeric block
+    int64_t nchunks = 0;
     fsparse_config cfg{};            // configuration that built this plan
 };
 
@@ -55,9 +55,9 @@ struct Batch {
     int64_t *h_len_off = nullptr;    // host [count+1]
     int64_t *h_nnz_off = nullptr;    // host [count+1]
     uint32_t *perm = nullptr;        // [total_len], k offset into the concatenation
-    uint32_t *tile_slot0 = nullptr;  // [ntiles+1]
+    uint32_t *chunk_slot0 = nullptr; // [nchunks+1]
     int numeric_tile = 4096;
-    int64_t ntiles = 0;
+    int64_t nchunks = 0;
 };
 
 // ---- errors ---------------------------------------------------------------
@@ -124,7 +124,7 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
                              int32_t n, const KeyLayout &key, const fsparse_config &cfg,
                              uint32_t *perm_out, DevStatus *st, Scratch &scratch, cudaStream_t s);
 
-// Run detection + slots + irank + irS + column counts + numeric tile bases
+// Run detection + slots + irank + irS + column counts + chunk slot bases
 // from a sorted perm (gathering the keys back from ii/jj).
 fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
                               int32_t n, const KeyLayout &key, Plan &plan, DevStatus *st,
@@ -134,18 +134,19 @@ fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len,
 fsparse_status exclusive_scan_u32(const uint32_t *counts, uint32_t *out, int64_t count,
                                   DevStatus *st, Scratch &scratch, cudaStream_t s);
 
-// Numeric fold prS[slot] over perm/tile bases; tail [nnz, cap) zero-filled.
-fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *tile_slot0, int64_t len,
-                              int64_t ntiles, int tile, const double *sr, double *prS,
-                              int64_t nnz, int64_t cap, cudaStream_t s);
+// Numeric fold prS[slot] over perm and the chunk slot bases; tail [nnz, cap)
+// zero-filled.  block_positions: 1024, 2048 or 4096.
+fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *chunk_slot0, int64_t len,
+                              int block_positions, const double *sr, double *prS, int64_t nnz,
+                              int64_t cap, cudaStream_t s);
 fsparse_status launch_adjoint(const int32_t *irank, int64_t len, const double *dprS, double *ds,
                               int64_t nnz, cudaStream_t s);
 fsparse_status launch_fill(int32_t *irS, double *prS, int64_t from, int64_t to, cudaStream_t s);
 fsparse_status launch_iota(uint32_t *perm, int64_t len, cudaStream_t s);
 fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t len,
                                    uint32_t offset, cudaStream_t s);
-fsparse_status launch_tile_heads(const uint32_t *perm, int64_t len, int tile, uint32_t *counts,
-                                 int64_t ntiles, cudaStream_t s);
+fsparse_status launch_chunk_heads(const uint32_t *perm, int64_t len, uint32_t *counts,
+                                  int64_t nchunks, cudaStream_t s);
 
 // Hybrid column-bucket path.  Returns FSPARSE_OK and sets *overflow when a
 // bucket does not fit; the caller then redoes the call with onesweep.

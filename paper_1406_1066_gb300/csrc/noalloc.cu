@@ -77,12 +77,12 @@ extern "C" fsparse_status fsparse_assemble_noalloc(const int32_t *ii, const int3
     const fsparse_config cfg{FSPARSE_SORT_ONESWEEP, 8, 16, 256, 8192, 1024};
     plan.cfg = cfg;
     plan.numeric_tile = cfg.numeric_tile;
-    plan.ntiles = (len + cfg.numeric_tile - 1) / cfg.numeric_tile;
+    plan.nchunks = (len + kChunk - 1) / kChunk;
     plan.irank = irank;
     plan.irS = irS;
     plan.jcS = jcS;
     if ((e = scratch.get(&plan.perm, (size_t)std::max<int64_t>(len, 1))) != FSPARSE_OK) return e;
-    if ((e = scratch.get(&plan.tile_slot0, (size_t)plan.ntiles + 1)) != FSPARSE_OK) return e;
+    if ((e = scratch.get(&plan.chunk_slot0, (size_t)plan.nchunks + 1)) != FSPARSE_OK) return e;
 
     if (len == 0) {
         FSP_CUDA(cudaMemsetAsync(jcS, 0, ((size_t)n + 1) * 4, s));
@@ -91,8 +91,8 @@ extern "C" fsparse_status fsparse_assemble_noalloc(const int32_t *ii, const int3
             return e;
         if ((e = emit_from_perm(ii, jj, len, m, n, plan.key, plan, d_st, scratch, s)) != FSPARSE_OK)
             return e;
-        if ((e = launch_numeric(plan.perm, plan.tile_slot0, len, plan.ntiles, plan.numeric_tile, sr, prS,
-                                0, 0, s)) != FSPARSE_OK)
+        if ((e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s)) !=
+            FSPARSE_OK)
             return e;
     }
     DevStatus h{};   // pageable stack copy: no pinned allocation

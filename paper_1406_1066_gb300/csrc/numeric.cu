@@ -2,8 +2,8 @@
 //
 // Numeric fold (Eq. (2.3) with the App. A insert order): the plan stores the
 // sorted order perm[p] = k, with kHeadBit on the first triplet of every run
-// (one run per CCS slot), and tile_slot0[q] = number of runs that start
-// before numeric tile q.  ONE thread folds each run from +0.0 in ascending
+// (one run per CCS slot), and chunk_slot0[q] = number of runs that start
+// before position q*kChunk.  ONE thread folds each run from +0.0 in ascending
 // position order -- which is ascending k, the paper's order -- so the result
 // is identical to the serial insert, bit for bit, for any launch shape.  No
 // atomics touch values.
@@ -24,37 +24,34 @@ __device__ __forceinline__ double gather(const double *__restrict__ sr, uint32_t
     return k < len ? __ldg(sr + k) : 0.0;
 }
 
-// Register-blocked fold.  Thread t of a tile owns IPT consecutive positions:
-// it loads their perm entries with 128-bit loads, issues all IPT value
-// gathers at once, and folds every run that starts in its chunk in
-// registers.  A run that crosses the chunk end continues through the leading
-// segments (positions before the first run head) of the following threads,
-// which are published in shared memory column-major (conflict-free), and,
-// at the tile end, through a prefetched halo of the next tile.
-template <int THREADS, int IPT>
+// Chunked fold.  Positions are cut into chunks of kChunk = 16; the plan keeps,
+// per chunk, the number of runs that start before it (chunk_slot0), so every
+// chunk is processed by one thread with no communication at all:
+//   * 128-bit loads of the chunk's perm entries;
+//   * positions before the chunk's first run head belong to a run that an
+//     earlier thread owns: skipped;
+//   * every run that starts in the chunk is folded in registers from +0.0 in
+//     ascending position order (= ascending k);
+//   * the chunk's last run continues past the chunk: the thread keeps reading
+//     perm (eight entries at a time, L1-resident since the neighbouring thread
+//     loaded them) and gathering values until the next run head.
+// Every value is gathered exactly once; no shared memory, no barriers.
+template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
     numeric_kernel(const uint32_t *__restrict__ perm, const double *__restrict__ sr,
-                   const uint32_t *__restrict__ tile_slot0, double *__restrict__ prS, int64_t len,
-                   int64_t ntiles, int64_t nnz) {
-    constexpr int NT = THREADS * IPT, HALO = 32;
-    __shared__ double s_lead[NT + HALO];     // [j * THREADS + t]: leading values of thread t
-    __shared__ uint8_t s_nlead[THREADS];     // leading-segment length of each thread
-    __shared__ uint8_t s_ends[THREADS];      // 1 if a run head lies in the thread's chunk
-    __shared__ uint32_t s_scan[THREADS / 32 + 1];
-    __shared__ int s_halo;                   // halo positions before the next head (HALO+1: none)
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                   const uint32_t *__restrict__ chunk_slot0, double *__restrict__ prS, int64_t len,
+                   int64_t nchunks, int64_t nnz) {
+    constexpr int C = kChunk;
     const bool vec = (reinterpret_cast<uintptr_t>(perm) & 15) == 0;
-    for (int64_t q = blockIdx.x; q < ntiles; q += gridDim.x) {
-        const int64_t P0 = q * NT;
-        const int cnt = (int)min64(NT, len - P0);
-        const int first = tid * IPT;
-        const int nval = max(0, min(IPT, cnt - first));
-        uint32_t pm[IPT];
-        if (nval == IPT && vec) {
+    for (int64_t q = blockIdx.x * (int64_t)THREADS + threadIdx.x; q < nchunks;
+         q += (int64_t)gridDim.x * THREADS) {
+        const int64_t p0 = q * C;
+        const int nval = (int)min64(C, len - p0);
+        uint32_t pm[C];
+        if (nval == C && vec) {
 #pragma unroll
-            for (int v = 0; v < IPT / 4; ++v) {
-                const uint4 x = reinterpret_cast<const uint4 *>(perm + P0 + first)[v];
+            for (int v = 0; v < C / 4; ++v) {
+                const uint4 x = __ldg(reinterpret_cast<const uint4 *>(perm + p0) + v);
                 pm[4 * v] = x.x;
                 pm[4 * v + 1] = x.y;
                 pm[4 * v + 2] = x.z;
@@ -62,112 +59,79 @@ __global__ void __launch_bounds__(THREADS)
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < IPT; ++i) pm[i] = i < nval ? perm[P0 + first + i] : kHeadBit;
+            for (int i = 0; i < C; ++i) pm[i] = i < nval ? __ldg(perm + p0 + i) : 0u;
         }
-        double v[IPT];
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) v[i] = i < nval ? gather(sr, pm[i], len) : 0.0;
         uint32_t hmask = 0;
 #pragma unroll
-        for (int i = 0; i < IPT; ++i)
+        for (int i = 0; i < C; ++i)
             if (i < nval && (pm[i] & kHeadBit)) hmask |= 1u << i;
-        const int lead = hmask ? __ffs(hmask) - 1 : nval;
+        if (hmask == 0) continue;   // the whole chunk lies inside an earlier thread's run
+        const int lead = __ffs(hmask) - 1;
+        int64_t slot = __ldg(chunk_slot0 + q);
+        double v[C];
 #pragma unroll
-        for (int i = 0; i < IPT; ++i)
-            if (i < lead) s_lead[i * THREADS + tid] = v[i];
-        s_nlead[tid] = (uint8_t)lead;
-        s_ends[tid] = hmask != 0 || nval < IPT;   // a short chunk is the end of the data
-        // The last warp prefetches the halo: where the tile's last run may go on.
-        if (warp == THREADS / 32 - 1) {
-            const int64_t hp = P0 + cnt + lane;
-            const bool in = cnt == NT && hp < len;
-            const uint32_t x = in ? perm[hp] : kHeadBit;
-            const uint32_t hm = __ballot_sync(0xffffffffu, x & kHeadBit);
-            const int end = hm ? __ffs(hm) - 1 : HALO + 1;   // HALO+1: the run goes past the halo
-            if (lane < (end > HALO ? HALO : end)) s_lead[NT + lane] = gather(sr, x, len);
-            if (lane == 0) s_halo = end;
-        }
-        uint32_t tile_heads;
-        const uint32_t excl = block_exclusive_scan<THREADS>(__popc(hmask), s_scan, &tile_heads);
-
-        // Runs that start in this chunk, folded in registers from +0.0.
-        int64_t slot = (int64_t)tile_slot0[q] + excl;
-        double acc = 0.0;
+        for (int i = 0; i < C; ++i) v[i] = (i >= lead && i < nval) ? gather(sr, pm[i], len) : 0.0;
+        double acc = 0.0;   // +0.0: the insert adds into zeroed storage
         bool open = false;
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) {
+        for (int i = 0; i < C; ++i) {
             if ((hmask >> i) & 1u) {
                 if (open && slot < nnz) prS[slot] = acc;
                 slot += open;
-                acc = 0.0;   // +0.0: the insert adds into zeroed storage
+                acc = 0.0;
                 open = true;
             }
             if (open && i < nval) acc += v[i];
         }
-        if (open) {
-            // Continue through the leading segments of the following threads.
-            bool done = nval < IPT;
-            int t = tid + 1;
-            for (; !done && t < THREADS; ++t) {
-                const int nl = s_nlead[t];
-                for (int j = 0; j < nl; ++j) acc += s_lead[j * THREADS + t];
-                done = s_ends[t];
-            }
-            if (!done) {
-                const int h = s_halo;
-                const int take = h > HALO ? HALO : h;
-                for (int j = 0; j < take; ++j) acc += s_lead[NT + j];
-                if (h > HALO) {
-                    // Longer than the halo: stream the rest, eight at a time, in order.
-                    int64_t g = P0 + cnt + HALO;
-                    while (g < len) {
-                        uint32_t x[8];
-                        int c = 0;
+        // Continue the last run past the chunk, in order, until the next head.
+        int64_t g = p0 + C;
+        while (nval == C && g < len) {
+            uint32_t x[8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) x[u] = g + u < len ? perm[g + u] : kHeadBit;
+            for (int u = 0; u < 8; ++u) x[u] = g + u < len ? __ldg(perm + g + u) : kHeadBit;
+            int c = 0;
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            if (c == u && !(x[u] & kHeadBit)) ++c;
-                        double w[8];
+            for (int u = 0; u < 8; ++u)
+                if (c == u && !(x[u] & kHeadBit)) ++c;
+            double w[8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) w[u] = u < c ? gather(sr, x[u], len) : 0.0;
-                        for (int u = 0; u < c; ++u) acc += w[u];
-                        if (c < 8) break;
-                        g += 8;
-                    }
-                }
-            }
-            if (slot < nnz) prS[slot] = acc;
+            for (int u = 0; u < 8; ++u) w[u] = u < c ? gather(sr, x[u], len) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < c) acc += w[u];
+            if (c < 8) break;
+            g += 8;
         }
-        __syncthreads();   // s_lead / s_nlead are reused by the next tile
+        if (slot < nnz) prS[slot] = acc;
     }
 }
 
-template <int THREADS, int IPT>
-static fsparse_status run_numeric(const uint32_t *perm, const uint32_t *tile_slot0, int64_t len,
-                                  int64_t ntiles, const double *sr, double *prS, int64_t nnz,
-                                  cudaStream_t s) {
-    auto kern = numeric_kernel<THREADS, IPT>;
+template <int THREADS>
+static fsparse_status run_numeric(const uint32_t *perm, const uint32_t *chunk_slot0, int64_t len,
+                                  const double *sr, double *prS, int64_t nnz, cudaStream_t s) {
+    auto kern = numeric_kernel<THREADS>;
+    const int64_t nchunks = (len + kChunk - 1) / kChunk;
     int per_sm = 0;
     FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0));
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sm_count(0) * std::max(per_sm, 1) * 8);
-    kern<<<(unsigned)grid, THREADS, 0, s>>>(perm, sr, tile_slot0, prS, len, ntiles, nnz);
+    const int64_t blocks = (nchunks + THREADS - 1) / THREADS;
+    const int64_t grid = std::min<int64_t>(blocks, (int64_t)sm_count(0) * std::max(per_sm, 1) * 16);
+    kern<<<(unsigned)grid, THREADS, 0, s>>>(perm, sr, chunk_slot0, prS, len, nchunks, nnz);
     FSP_LAUNCHED();
     return FSPARSE_OK;
 }
 
-fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *tile_slot0, int64_t len,
-                              int64_t ntiles, int tile, const double *sr, double *prS,
-                              int64_t nnz, int64_t cap, cudaStream_t s) {
+fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *chunk_slot0, int64_t len,
+                              int block_positions, const double *sr, double *prS, int64_t nnz,
+                              int64_t cap, cudaStream_t s) {
     fsparse_status e = FSPARSE_OK;
     // Writes are bounded by the output capacity (nnz is unknown to the host when
     // the fold is fused into the symbolic call; then the caller passes cap = len).
     const int64_t nnz_bound = cap > 0 ? cap : len;
     if (len > 0) {
-        if (tile == 1024) e = run_numeric<128, 8>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
-        else if (tile == 2048) e = run_numeric<128, 16>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
-        else if (tile == 4096) e = run_numeric<256, 16>(perm, tile_slot0, len, ntiles, sr, prS, nnz_bound, s);
-        else return set_error(FSPARSE_ERR_ARG, "unsupported numeric tile");
+        if (block_positions == 1024) e = run_numeric<64>(perm, chunk_slot0, len, sr, prS, nnz_bound, s);
+        else if (block_positions == 2048) e = run_numeric<128>(perm, chunk_slot0, len, sr, prS, nnz_bound, s);
+        else if (block_positions == 4096) e = run_numeric<256>(perm, chunk_slot0, len, sr, prS, nnz_bound, s);
+        else return set_error(FSPARSE_ERR_ARG, "unsupported numeric block size");
         if (e != FSPARSE_OK) return e;
     }
     if (cap > nnz) return launch_fill(nullptr, prS, nnz, cap, s);
@@ -256,27 +220,23 @@ fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t l
     return FSPARSE_OK;
 }
 
-// Run heads per numeric tile (their exclusive scan is tile_slot0).
-__global__ void tile_heads_kernel(const uint32_t *__restrict__ perm, int64_t len, int tile,
-                                  uint32_t *counts, int64_t ntiles) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_id = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = warp_id; q < ntiles; q += nwarps) {
-        const int64_t p0 = q * tile, p1 = min64(p0 + tile, len);
+// Run heads per chunk of kChunk positions (their exclusive scan is chunk_slot0).
+__global__ void chunk_heads_kernel(const uint32_t *__restrict__ perm, int64_t len,
+                                   uint32_t *__restrict__ counts, int64_t nchunks) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunks;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = q * kChunk, p1 = min64(p0 + kChunk, len);
         uint32_t c = 0;
-        for (int64_t p = p0 + lane; p < p1; p += 32) c += (perm[p] >> 31);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0) counts[q] = c;
+        for (int64_t p = p0; p < p1; ++p) c += perm[p] >> 31;
+        counts[q] = c;
     }
 }
 
-fsparse_status launch_tile_heads(const uint32_t *perm, int64_t len, int tile, uint32_t *counts,
-                                 int64_t ntiles, cudaStream_t s) {
-    if (ntiles == 0) return FSPARSE_OK;
-    const int grid = (int)std::min<int64_t>((ntiles * 32 + 255) / 256, (int64_t)sm_count(0) * 8);
-    tile_heads_kernel<<<std::max(grid, 1), 256, 0, s>>>(perm, len, tile, counts, ntiles);
+fsparse_status launch_chunk_heads(const uint32_t *perm, int64_t len, uint32_t *counts,
+                                  int64_t nchunks, cudaStream_t s) {
+    if (nchunks == 0) return FSPARSE_OK;
+    const int grid = (int)std::min<int64_t>((nchunks + 255) / 256, (int64_t)sm_count(0) * 8);
+    chunk_heads_kernel<<<std::max(grid, 1), 256, 0, s>>>(perm, len, counts, nchunks);
     FSP_LAUNCHED();
     return FSPARSE_OK;
 }

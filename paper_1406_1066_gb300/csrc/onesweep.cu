@@ -20,7 +20,7 @@
 //      neighbours (a new run starts where the key changes: the collision
 //      detection of Part 3), numbers the runs with a block scan plus
 //      look-back, and writes irank (Eq. (2.2)), irS, the per-column unique
-//      counts (scanned into jcS, Part 4) and the numeric tile bases.
+//      counts (scanned into jcS, Part 4) and the numeric chunk slot bases.
 #include <algorithm>
 
 #include "common.cuh"
@@ -359,7 +359,7 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
 }
 
 // ----------------------------------------------------------------------------
-// Emit: runs, slots, irank, irS, column counts and numeric tile bases.
+// Emit: runs, slots, irank, irS, column counts and numeric chunk slot bases.
 struct EmitArgs {
     const int32_t *ii, *jj;
     int32_t m, n;
@@ -367,9 +367,8 @@ struct EmitArgs {
     uint32_t *perm;          // in: sorted k, out: k | kHeadBit on run heads
     int32_t *irank, *irS;
     uint32_t *colcnt;        // [n] unique pairs per column (zeroed)
-    uint32_t *tile_slot0;    // [ntiles_num + 1]
-    int num_shift;           // log2 of the numeric tile
-    int64_t ntiles_num;
+    uint32_t *chunk_slot0;   // [nchunks + 1]
+    int64_t nchunks;
     int64_t len;
     uint32_t *look;
     uint32_t *ticket;
@@ -467,11 +466,10 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
             }
             ++run_cnt;
         }
-        if ((p & ((1ll << a.num_shift) - 1)) == 0)
-            a.tile_slot0[p >> a.num_shift] = head ? slot : slot + 1;
+        if ((p & (kChunk - 1)) == 0) a.chunk_slot0[p >> kChunkShift] = head ? slot : slot + 1;
         if (p == a.len - 1) {
             a.st->nnz = slot + 1;
-            a.tile_slot0[a.ntiles_num] = slot + 1;
+            a.chunk_slot0[a.nchunks] = slot + 1;
         }
     }
     if (run_cnt) atomicAdd(&a.colcnt[run_col], run_cnt);
@@ -485,12 +483,6 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
         for (int i = 0; i < ITEMS; ++i)
             if (p0 + i < a.len) a.perm[p0 + i] = out[i];
     }
-}
-
-static int log2i(int x) {
-    int r = 0;
-    while ((1 << r) < x) ++r;
-    return r;
 }
 
 fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
@@ -517,9 +509,8 @@ fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len,
         a.irank = plan.irank;
         a.irS = plan.irS;
         a.colcnt = colcnt;
-        a.tile_slot0 = plan.tile_slot0;
-        a.num_shift = log2i(plan.numeric_tile);
-        a.ntiles_num = plan.ntiles;
+        a.chunk_slot0 = plan.chunk_slot0;
+        a.nchunks = plan.nchunks;
         a.len = len;
         a.look = look;
         a.ticket = ticket;
