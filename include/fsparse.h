@@ -95,7 +95,10 @@ fsparse_status fsparse_plan_info(fsparse_plan plan, int32_t *m, int32_t *n, int6
 
 /* Plan-owned device arrays, valid until fsparse_plan_destroy; read only for
    the caller.  irank int32[len] (Eq. (2.2)), jcS int32[n+1], irS int32[cap].
-   Any output pointer may be NULL.  Host only. */
+   Any output pointer may be NULL.  irank is derived from the plan's sorted
+   order the first time it is requested: a non-NULL irank argument on the
+   first call launches one kernel on the legacy default stream and waits for
+   it (later calls return at once). */
 fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank,
                                    const int32_t **jcS, const int32_t **irS);
 
@@ -119,7 +122,9 @@ fsparse_status fsparse_numeric(fsparse_plan plan, const double *sr, double *prS,
 
 /* Adjoint (transpose) of the numeric map, which is linear in sr (Eq. (2.3)):
    ds[k] = dprS[irank[k]] for k < len.  dprS device double[>= nnz], ds device
-   double[len].  Exact (a gather, no rounding).  No sync, no allocation. */
+   double[len].  Exact (a gather, no rounding).  No sync, no allocation; the
+   first adjoint call on a plan whose irank was never requested also
+   launches the kernel that derives irank, on `stream`. */
 fsparse_status fsparse_numeric_adjoint(fsparse_plan plan, const double *dprS, double *ds,
                                        void *stream);
 

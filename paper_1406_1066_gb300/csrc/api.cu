@@ -161,14 +161,13 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     *folded = false;
     fsparse_status e;
     if (cfg.strategy == FSPARSE_SORT_BUCKET && bucket_supported(len, plan.n, plan.key, cfg)) {
-        e = bucket_symbolic(ii, jj, sr, prS, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s);
-        if (e == FSPARSE_OK) *folded = sr != nullptr;
-        return e;
+        e = bucket_symbolic(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s);
+    } else {
+        if ((e = onesweep_sort(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan.perm, d_st, scratch, s)) != FSPARSE_OK)
+            return e;
+        e = emit_from_perm(ii, jj, len, plan.m, plan.n, plan.key, plan, d_st, scratch, s);
     }
-    if ((e = onesweep_sort(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan.perm, d_st, scratch, s)) != FSPARSE_OK)
-        return e;
-    if ((e = emit_from_perm(ii, jj, len, plan.m, plan.n, plan.key, plan, d_st, scratch, s)) != FSPARSE_OK)
-        return e;
+    if (e != FSPARSE_OK) return e;
     if (sr) {
         e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s);
         if (e == FSPARSE_OK) *folded = true;
@@ -294,10 +293,28 @@ fsparse_status fsparse_plan_info(fsparse_plan plan, int32_t *m, int32_t *n, int6
     return FSPARSE_OK;
 }
 
+// irank is derived from perm the first time it is needed.
+static fsparse_status ensure_irank(Plan &p, cudaStream_t s, bool sync) {
+    if (p.irank_ready) return FSPARSE_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p.device) cudaSetDevice(p.device);
+    fsparse_status e = launch_irank(p.perm, p.chunk_slot0, p.len, p.irank, s);
+    if (e == FSPARSE_OK && sync && cudaStreamSynchronize(s) != cudaSuccess)
+        e = cuda_error(cudaGetLastError(), "cudaStreamSynchronize");
+    if (cur != p.device) cudaSetDevice(cur);
+    if (e == FSPARSE_OK) p.irank_ready = true;
+    return e;
+}
+
 fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank, const int32_t **jcS,
                                    const int32_t **irS) {
     if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
-    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    if (irank) {
+        fsparse_status e = ensure_irank(p, nullptr, true);
+        if (e != FSPARSE_OK) return e;
+    }
     if (irank) *irank = p.irank;
     if (jcS) *jcS = p.jcS;
     if (irS) *irS = p.irS;
@@ -326,8 +343,10 @@ fsparse_status fsparse_numeric(fsparse_plan plan, const double *sr, double *prS,
 
 fsparse_status fsparse_numeric_adjoint(fsparse_plan plan, const double *dprS, double *ds, void *stream) {
     if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
-    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
     if (p.len > 0 && (!dprS || !ds)) return set_error(FSPARSE_ERR_ARG, "NULL array");
+    fsparse_status e = ensure_irank(p, as_stream(stream), false);
+    if (e != FSPARSE_OK) return e;
     return launch_adjoint(p.irank, p.len, dprS, ds, p.nnz, as_stream(stream));
 }
 

@@ -21,9 +21,9 @@
 //                keeps no order inside a block), detects runs by comparing
 //                neighbours (the collision detection of Part 3), numbers the
 //                slots with one decoupled look-back across buckets, and writes
-//                perm, irank, irS, jcS (Part 4's prefix, per bucket column),
-//                the numeric chunk slot bases and -- in a full assembly -- prS by
-//                folding each run from +0.0 in ascending k.
+//                perm, irS, jcS (Part 4's prefix, per bucket column),
+//                and the numeric chunk slot bases (the values are folded by
+//                the numeric kernel afterwards).
 //
 // A bucket above the kernel's capacity, or a run longer than kRunSortMax,
 // sets DevStatus::overflow; the host then redoes the call with the global
@@ -39,6 +39,7 @@ namespace fsp {
 constexpr int64_t kMaxBuckets = 32768;
 constexpr int kMaxColBits = 12;     // 2^cs column counters in shared memory
 constexpr int kRunSortMax = 128;    // longest run re-sorted by one thread
+constexpr int kRowBits = 1 << 16;   // row ranges up to this are compressed to dense ranks
 
 struct BucketShape {
     int cs = 0;        // low column bits kept inside a bucket
@@ -135,10 +136,8 @@ struct BucketEmitArgs {
     int cs, rb, kb;
     int32_t n;
     int64_t len;
-    const double *sr;      // NULL: symbolic only
-    double *prS;
     uint32_t *perm;
-    int32_t *irank, *irS, *jcS;
+    int32_t *irS, *jcS;
     uint32_t *chunk_slot0;
     int64_t nchunks;
     uint32_t *look;
@@ -155,7 +154,10 @@ struct BucketSmem {
     static constexpr size_t bytes_b = std::max<size_t>((size_t)WARPS * 256 * 4, (size_t)(1 << kMaxColBits) * 4);
     static constexpr size_t off_a = (size_t)CAP * 8;
     static constexpr size_t off_b = off_a + bytes_a;
-    static constexpr size_t off_local = off_b + bytes_b;
+    // Region C: row bitmap (kRowBits bits) and its u16 prefix counts.
+    static constexpr size_t off_bits = off_b + bytes_b;
+    static constexpr size_t off_pref = off_bits + (size_t)(kRowBits / 32) * 4;
+    static constexpr size_t off_local = off_pref + (size_t)(kRowBits / 32) * 2;
     static constexpr size_t off_scan = off_local + 256 * 4;
     static constexpr size_t off_misc = off_scan + (WARPS + 2) * 4;
     static constexpr size_t bytes = off_misc + 16 * 4;
@@ -164,7 +166,7 @@ struct BucketSmem {
 __device__ __forceinline__ int bits_of(uint32_t v) { return v ? 32 - __clz(v) : 0; }
 
 template <int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) {
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(BucketEmitArgs a) {
     using S = BucketSmem<THREADS, IPT>;
     constexpr int CAP = S::CAP, WARPS = S::WARPS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -173,6 +175,8 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
     uint16_t *s_hpos = reinterpret_cast<uint16_t *>(smem + S::off_a);    // after the sort
     uint32_t *s_wm = reinterpret_cast<uint32_t *>(smem + S::off_b);      // sort
     uint32_t *s_col = reinterpret_cast<uint32_t *>(smem + S::off_b);     // after the sort
+    uint32_t *s_bits = reinterpret_cast<uint32_t *>(smem + S::off_bits);
+    uint16_t *s_pref = reinterpret_cast<uint16_t *>(smem + S::off_pref);
     uint32_t *s_local = reinterpret_cast<uint32_t *>(smem + S::off_local);
     uint32_t *s_scan = reinterpret_cast<uint32_t *>(smem + S::off_scan);
     uint32_t *s_misc = reinterpret_cast<uint32_t *>(smem + S::off_misc);
@@ -193,14 +197,14 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
     const uint64_t kmask = (1ull << kb) - 1;
 
     if (nx > CAP || nx < 0) {   // does not fit: flag it, keep the look-back chain moving
-        if (tid == 0) {
-            atomicOr(&a.st->overflow, 1u);
-            if (x == 0) {
-                st_release(a.look, kFlagInc);
-            } else {
-                st_release(a.look + x, kFlagAgg);
-                const uint32_t e = lookback_exclusive(a.look, 1, x, a.st);
-                st_release(a.look + x, kFlagInc | e);
+        if (warp == 0) {
+            if (lane == 0) {
+                atomicOr(&a.st->overflow, 1u);
+                st_release(a.look + x, x == 0 ? kFlagInc : kFlagAgg);
+            }
+            if (x > 0) {
+                const uint32_t e = warp_lookback_exclusive(a.look, 1, x, a.st);
+                if (lane == 0) st_release(a.look + x, kFlagInc | e);
             }
         }
         return;
@@ -233,16 +237,49 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
     }
     __syncthreads();
     const uint32_t row_lo = nx ? s_misc[1] : 0u;
-    const int rbits = bits_of(nx ? s_misc[2] - row_lo : 0u);
+    const uint32_t range = nx ? s_misc[2] - row_lo + 1 : 0u;
+    // Rows of a bucket are compressed to dense ranks when their range fits the
+    // bitmap (mesh-like data: a few hundred distinct rows spread over ~2^15),
+    // which shortens the sort key; otherwise row - row_lo is used as is.
+    const bool dense = range > 0 && range <= (uint32_t)kRowBits;
+    int rbits;
+    if (dense) {
+        constexpr int WORDS = kRowBits / 32, WPT = WORDS / THREADS;
+        for (int w = tid; w < WORDS; w += THREADS) s_bits[w] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            if (valid[i]) {
+                const uint32_t r = (uint32_t)((pk[i] >> kb) & ((1ull << rb) - 1)) - row_lo;
+                atomicOr(&s_bits[r >> 5], 1u << (r & 31));
+            }
+        }
+        __syncthreads();
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) c += __popc(s_bits[tid * WPT + j]);
+        uint32_t distinct;
+        uint32_t run = block_exclusive_scan<THREADS>(c, s_scan, &distinct);
+#pragma unroll
+        for (int j = 0; j < WPT; ++j) {
+            s_pref[tid * WPT + j] = (uint16_t)run;
+            run += __popc(s_bits[tid * WPT + j]);
+        }
+        __syncthreads();
+        rbits = bits_of(distinct - 1);
+    } else {
+        rbits = bits_of(range ? range - 1 : 0u);
+    }
     const int npass = (a.cs + rbits + 7) / 8;
-    // Sort key inside the bucket: (column low bits, row - row_lo), then k below it.
+    // Sort key inside the bucket: (column low bits, row rank), then k below it.
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         if (valid[i]) {
             const uint64_t w = pk[i];
-            const uint64_t row = ((w >> kb) & ((1ull << rb) - 1)) - row_lo;
+            uint32_t row = (uint32_t)((w >> kb) & ((1ull << rb) - 1)) - row_lo;
+            if (dense) row = s_pref[row >> 5] + __popc(s_bits[row >> 5] & ((1u << (row & 31)) - 1u));
             const uint64_t lowcol = w >> (kb + rb);
-            pk[i] = ((((lowcol << rbits) | row)) << kb) | (w & kmask);
+            pk[i] = (((lowcol << rbits) | row) << kb) | (w & kmask);
         }
     }
 
@@ -320,6 +357,16 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
     }
     if (tid == 0) s_hpos[U] = (uint16_t)nx;
     for (int c = tid; c < (1 << a.cs); c += THREADS) s_col[c] = 0;
+    // Slot base of this bucket: warp 0 looks back over earlier buckets and
+    // publishes the inclusive prefix at once, before the run sort below.
+    if (warp == 0) {
+        uint32_t e = 0;
+        if (x > 0) {
+            e = warp_lookback_exclusive(a.look, 1, x, a.st);
+            if (lane == 0) st_release(a.look + x, kFlagInc | (e + U));
+        }
+        if (lane == 0) s_misc[3] = e;
+    }
     __syncthreads();
 
     // Ascending k inside every run (the scatter kept no order within a block).
@@ -339,18 +386,10 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
             s_w[q + 1] = v;
         }
     }
-    if (tid == 0) {
-        uint32_t e = 0;
-        if (x > 0) {
-            e = lookback_exclusive(a.look, 1, x, a.st);
-            st_release(a.look + x, kFlagInc | (e + U));
-        }
-        s_misc[3] = e;
-    }
     __syncthreads();
     const uint32_t E = s_misc[3];
 
-    // perm, irank, irS, column counts, chunk slot bases (warp-striped).
+    // perm, irS, column counts, chunk slot bases (warp-striped).
     const uint64_t rmaskx = (1ull << rbits) - 1;
     {
         uint32_t before = wbase;   // heads at earlier positions
@@ -367,9 +406,17 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
             const uint64_t sk = v >> kb;
             const int64_t gp = b0 + p;
             a.perm[gp] = k | (head ? kHeadBit : 0u);
-            if (in_range(k, a.len, a.st)) a.irank[k] = (int32_t)slot;
             if (head) {
-                if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)((sk & rmaskx) + row_lo);
+                uint32_t row = (uint32_t)(sk & rmaskx);
+            if (dense) {   // row of dense rank `row`: word by binary search, bit by __fns
+                int lo = 0, hi = kRowBits / 32 - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_pref[mid] <= row) lo = mid; else hi = mid - 1;
+                }
+                row = (uint32_t)lo * 32 + __fns(s_bits[lo], 0, (int)(row - s_pref[lo]) + 1);
+            }
+            if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)(row + row_lo);
                 const uint32_t lowcol = (uint32_t)(sk >> rbits);
                 if (in_range(lowcol, ncols, a.st)) atomicAdd(&s_col[lowcol], 1u);
             }
@@ -377,31 +424,6 @@ __global__ void __launch_bounds__(THREADS) bucket_emit_kernel(BucketEmitArgs a) 
         }
     }
 
-    // Fused numeric fold: every run from +0.0 in ascending k, gathering the
-    // values straight from sr (eight independent loads at a time).
-    if (a.sr != nullptr) {
-        for (uint32_t h = tid; h < U; h += THREADS) {
-            const int lo = s_hpos[h], hi = s_hpos[h + 1];
-            double acc = 0.0;   // +0.0: the insert adds into zeroed storage
-            for (int p = lo; p < hi; p += 8) {
-                const int c = min(8, hi - p);
-                double w[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    w[u] = 0.0;
-                    if (u < c) {
-                        const uint32_t k = (uint32_t)(s_w[p + u] & kmask);
-                        w[u] = k < a.len ? __ldg(a.sr + k) : 0.0;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (u < c) acc += w[u];
-            }
-            const int64_t dst = (int64_t)E + h;
-            if (in_range(dst, a.len, a.st)) a.prS[dst] = acc;
-        }
-    }
     __syncthreads();
 
     // jcS of this bucket's columns: E + exclusive prefix of the unique counts.
@@ -442,8 +464,8 @@ static fsparse_status run_emit(const BucketEmitArgs &a, int64_t nb, cudaStream_t
     return FSPARSE_OK;
 }
 
-fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr, double *prS,
-                               int64_t len, int32_t m, int32_t n, const KeyLayout &key,
+fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                               int32_t n, const KeyLayout &key,
                                const fsparse_config &cfg, Plan &plan, DevStatus *st, Scratch &scratch,
                                cudaStream_t s) {
     BucketShape sh;
@@ -486,10 +508,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const doubl
     a.kb = sh.kb;
     a.n = n;
     a.len = len;
-    a.sr = sr;
-    a.prS = prS;
     a.perm = plan.perm;
-    a.irank = plan.irank;
     a.irS = plan.irS;
     a.jcS = plan.jcS;
     a.chunk_slot0 = plan.chunk_slot0;

@@ -89,6 +89,44 @@ __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t *word, int
     return excl;
 }
 
+// Warp-cooperative version of lookback_exclusive: all 32 lanes of the calling
+// warp take part and inspect 32 predecessors per step (lane i looks at
+// tile-1-i), so a walk over many aggregate-only predecessors costs one load
+// latency per 32 of them.  Every lane returns the same value.  Bounded like
+// lookback_exclusive.
+__device__ __forceinline__ uint32_t warp_lookback_exclusive(const uint32_t *word, int64_t stride,
+                                                            int64_t tile, DevStatus *st) {
+    const int lane = threadIdx.x & 31;
+    uint32_t excl = 0;
+    for (int64_t hi = tile - 1; hi >= 0; hi -= 32) {
+        const int64_t t = hi - lane;
+        const bool have = t >= 0;
+        uint32_t v = have ? ld_acquire(word + t * stride) : kFlagInc;
+        int spins = 0;
+        uint32_t need;
+        while (true) {
+            const uint32_t inc = __ballot_sync(0xffffffffu, have && (v & kFlagMask) == kFlagInc);
+            const uint32_t ready = __ballot_sync(0xffffffffu, !have || (v & kFlagMask) != 0);
+            need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xffffffffu;   // lanes up to the nearest inclusive
+            if (need == 0) need = 0xffffffffu;                              // (inclusive in lane 31: all lanes)
+            if ((ready & need) == need) break;
+            if (++spins > kSpinLimit) {
+                if (lane == 0) atomicOr(&st->timeout, 1u);
+                return excl;
+            }
+            if (spins > 8) __nanosleep(spins > 64 ? 256 : 32);
+            if (have && (v & kFlagMask) == 0) v = ld_acquire(word + t * stride);
+        }
+        const uint32_t inc = __ballot_sync(0xffffffffu, have && (v & kFlagMask) == kFlagInc);
+        uint32_t part = ((need >> lane) & 1u) && have ? (v & kValueMask) : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        excl += part;
+        if (inc) break;
+    }
+    return excl;
+}
+
 // Block-wide exclusive scan of one uint32 per thread; returns the total in
 // *total.  `scratch` needs THREADS/32 + 1 words of shared memory.
 template <int THREADS>

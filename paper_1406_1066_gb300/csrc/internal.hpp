@@ -38,7 +38,8 @@ struct Plan {
     int32_t m = 0, n = 0;
     int64_t len = 0, nnz = 0, cap = 0;
     KeyLayout key;
-    int32_t *irank = nullptr;        // [len]
+    int32_t *irank = nullptr;        // [len], filled on first request (irank_ready)
+    bool irank_ready = false;
     int32_t *jcS = nullptr;          // [n+1]
     int32_t *irS = nullptr;          // [max(len, nzmax, 1)]
     uint32_t *perm = nullptr;        // [len] sorted position -> k, kHeadBit on run heads
@@ -141,6 +142,8 @@ fsparse_status launch_numeric(const uint32_t *perm, const uint32_t *chunk_slot0,
                               int64_t cap, cudaStream_t s);
 fsparse_status launch_adjoint(const int32_t *irank, int64_t len, const double *dprS, double *ds,
                               int64_t nnz, cudaStream_t s);
+fsparse_status launch_irank(const uint32_t *perm, const uint32_t *chunk_slot0, int64_t len,
+                            int32_t *irank, cudaStream_t s);
 fsparse_status launch_fill(int32_t *irS, double *prS, int64_t from, int64_t to, cudaStream_t s);
 fsparse_status launch_iota(uint32_t *perm, int64_t len, cudaStream_t s);
 fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t len,
@@ -150,10 +153,9 @@ fsparse_status launch_chunk_heads(const uint32_t *perm, int64_t len, uint32_t *c
 
 // Hybrid column-bucket path.  Returns FSPARSE_OK and sets *overflow when a
 // bucket does not fit; the caller then redoes the call with onesweep.
-fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr,
-                               double *prS, int64_t len, int32_t m, int32_t n,
-                               const KeyLayout &key, const fsparse_config &cfg, Plan &plan,
-                               DevStatus *st, Scratch &scratch, cudaStream_t s);
+fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                               int32_t n, const KeyLayout &key, const fsparse_config &cfg,
+                               Plan &plan, DevStatus *st, Scratch &scratch, cudaStream_t s);
 bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg);
 
 }  // namespace fsp

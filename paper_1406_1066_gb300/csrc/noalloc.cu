@@ -94,6 +94,7 @@ extern "C" fsparse_status fsparse_assemble_noalloc(const int32_t *ii, const int3
         if ((e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s)) !=
             FSPARSE_OK)
             return e;
+        if ((e = launch_irank(plan.perm, plan.chunk_slot0, len, irank, s)) != FSPARSE_OK) return e;
     }
     DevStatus h{};   // pageable stack copy: no pinned allocation
     FSP_CUDA(cudaMemcpyAsync(&h, d_st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));

@@ -17,6 +17,13 @@
 
 namespace fsp {
 
+// +0.0 + v, exactly, without an FP64 add (FP64 adds are scarce on GB300):
+// equal to v for every v except -0.0, which becomes +0.0 (a NaN stays NaN).
+__device__ __forceinline__ double plus_zero(double v) {
+    const unsigned long long b = __double_as_longlong(v);
+    return __longlong_as_double(b == 0x8000000000000000ull ? 0ull : b);
+}
+
 // Value of triplet x (head bit ignored); an index beyond len, which a valid
 // plan never holds, reads as 0 instead of faulting.
 __device__ __forceinline__ double gather(const double *__restrict__ sr, uint32_t x, int64_t len) {
@@ -71,24 +78,33 @@ __global__ void __launch_bounds__(THREADS)
         double v[C];
 #pragma unroll
         for (int i = 0; i < C; ++i) v[i] = (i >= lead && i < nval) ? gather(sr, pm[i], len) : 0.0;
-        double acc = 0.0;   // +0.0: the insert adds into zeroed storage
+        // Each run: (((+0.0 + v0) + v1) + ...), the first add done as plus_zero.
+        double acc = 0.0;
         bool open = false;
 #pragma unroll
         for (int i = 0; i < C; ++i) {
             if ((hmask >> i) & 1u) {
                 if (open && slot < nnz) prS[slot] = acc;
                 slot += open;
-                acc = 0.0;
+                acc = plus_zero(v[i]);
                 open = true;
+            } else if (open && i < nval) {
+                acc += v[i];
             }
-            if (open && i < nval) acc += v[i];
         }
         // Continue the last run past the chunk, in order, until the next head.
         int64_t g = p0 + C;
         while (nval == C && g < len) {
             uint32_t x[8];
+            if (g + 8 <= len && vec) {   // g is a multiple of 8: two aligned 16-byte loads
+                const uint4 a0 = __ldg(reinterpret_cast<const uint4 *>(perm + g));
+                const uint4 a1 = __ldg(reinterpret_cast<const uint4 *>(perm + g) + 1);
+                x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+                x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+            } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = g + u < len ? __ldg(perm + g + u) : kHeadBit;
+                for (int u = 0; u < 8; ++u) x[u] = g + u < len ? __ldg(perm + g + u) : kHeadBit;
+            }
             int c = 0;
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -168,6 +184,36 @@ fsparse_status launch_adjoint(const int32_t *irank, int64_t len, const double *d
     const int64_t work = vec ? (len + 3) / 4 : len;
     const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count(0) * 8);
     adjoint_kernel<<<std::max(grid, 1), 256, 0, s>>>(irank, len, dprS, ds, vec, nnz);
+    FSP_LAUNCHED();
+    return FSPARSE_OK;
+}
+
+// irank from the sorted order: irank[perm[p]] = slot of position p, where the
+// slot of p is the number of run heads at positions <= p, minus one.  One
+// thread per kChunk positions, starting from the chunk's slot base.
+__global__ void irank_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ chunk_slot0,
+                             int64_t len, int32_t *__restrict__ irank) {
+    const int64_t nchunks = (len + kChunk - 1) / kChunk;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunks;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = q * kChunk;
+        uint32_t slot = chunk_slot0[q] - 1;
+        const int nval = (int)min64(kChunk, len - p0);
+        for (int i = 0; i < nval; ++i) {
+            const uint32_t x = perm[p0 + i];
+            slot += x >> 31;
+            const uint32_t k = x & kIndexMask;
+            if (k < len) irank[k] = (int32_t)slot;
+        }
+    }
+}
+
+fsparse_status launch_irank(const uint32_t *perm, const uint32_t *chunk_slot0, int64_t len,
+                            int32_t *irank, cudaStream_t s) {
+    if (len == 0) return FSPARSE_OK;
+    const int64_t nchunks = (len + kChunk - 1) / kChunk;
+    const int grid = (int)std::min<int64_t>((nchunks + 255) / 256, (int64_t)sm_count(0) * 16);
+    irank_kernel<<<std::max(grid, 1), 256, 0, s>>>(perm, chunk_slot0, len, irank);
     FSP_LAUNCHED();
     return FSPARSE_OK;
 }

@@ -19,8 +19,9 @@
 //   4. the emit kernel gathers each sorted triplet's (i, j) back, compares
 //      neighbours (a new run starts where the key changes: the collision
 //      detection of Part 3), numbers the runs with a block scan plus
-//      look-back, and writes irank (Eq. (2.2)), irS, the per-column unique
-//      counts (scanned into jcS, Part 4) and the numeric chunk slot bases.
+//      look-back, and writes irS, the per-column unique counts (scanned into
+//      jcS, Part 4) and the numeric chunk slot bases; irank (Eq. (2.2)) is
+//      derived from perm on first request.
 #include <algorithm>
 
 #include "common.cuh"
@@ -359,13 +360,13 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
 }
 
 // ----------------------------------------------------------------------------
-// Emit: runs, slots, irank, irS, column counts and numeric chunk slot bases.
+// Emit: runs, slots, irS, column counts and numeric chunk slot bases.
 struct EmitArgs {
     const int32_t *ii, *jj;
     int32_t m, n;
     int rb;
     uint32_t *perm;          // in: sorted k, out: k | kHeadBit on run heads
-    int32_t *irank, *irS;
+    int32_t *irS;
     uint32_t *colcnt;        // [n] unique pairs per column (zeroed)
     uint32_t *chunk_slot0;   // [nchunks + 1]
     int64_t nchunks;
@@ -426,17 +427,15 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
     }
     uint32_t tile_heads;
     const uint32_t mine = block_exclusive_scan<THREADS>(__popc(heads), s_scan, &tile_heads);
-    if (tid == 0) {
+    if (tid < 32) {
         uint32_t *word = a.look + tile;
         uint32_t excl = 0;
-        if (tile == 0) {
-            st_release(word, kFlagInc | tile_heads);
-        } else {
-            st_release(word, kFlagAgg | tile_heads);
-            excl = lookback_exclusive(a.look, 1, tile, a.st);
-            st_release(word, kFlagInc | (excl + tile_heads));
+        if (tid == 0) st_release(word, (tile == 0 ? kFlagInc : kFlagAgg) | tile_heads);
+        if (tile > 0) {
+            excl = warp_lookback_exclusive(a.look, 1, tile, a.st);
+            if (tid == 0) st_release(word, kFlagInc | (excl + tile_heads));
         }
-        s_excl = excl;
+        if (tid == 0) s_excl = excl;
     }
     __syncthreads();
 
@@ -453,7 +452,6 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
         const bool head = (heads >> i) & 1u;
         slot += head;
         const uint32_t kk = k[i] & kIndexMask;
-        if (in_range(kk, a.len, a.st)) a.irank[kk] = (int32_t)slot;
         out[i] = kk | (head ? kHeadBit : 0u);
         if (head) {
             const uint32_t row = (uint32_t)(key[i] & ((1ull << a.rb) - 1));
@@ -506,7 +504,6 @@ fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len,
         a.n = n;
         a.rb = key.rb;
         a.perm = plan.perm;
-        a.irank = plan.irank;
         a.irS = plan.irS;
         a.colcnt = colcnt;
         a.chunk_slot0 = plan.chunk_slot0;

@@ -33,17 +33,15 @@ __global__ void __launch_bounds__(THREADS)
     }
     uint32_t tile_sum;
     const uint32_t mine = block_exclusive_scan<THREADS>(sum, s_scan, &tile_sum);
-    if (tid == 0) {
+    if (tid < 32) {
         uint32_t *word = look + tile;
         uint32_t excl = 0;
-        if (tile == 0) {
-            st_release(word, kFlagInc | tile_sum);
-        } else {
-            st_release(word, kFlagAgg | tile_sum);
-            excl = lookback_exclusive(look, 1, tile, st);
-            st_release(word, kFlagInc | (excl + tile_sum));
+        if (tid == 0) st_release(word, (tile == 0 ? kFlagInc : kFlagAgg) | tile_sum);
+        if (tile > 0) {
+            excl = warp_lookback_exclusive(look, 1, tile, st);
+            if (tid == 0) st_release(word, kFlagInc | (excl + tile_sum));
         }
-        s_excl = excl;
+        if (tid == 0) s_excl = excl;
     }
     __syncthreads();
     uint32_t run = s_excl + mine;

@@ -119,10 +119,13 @@ def fsparse_plan_info(plan: int) -> Tuple[int, int, int, int, int]:
     return m.value, n.value, L.value, nnz.value, cap.value
 
 
-def fsparse_plan_arrays(plan: int) -> Tuple[int, int, int]:
+def fsparse_plan_arrays(plan: int, irank: bool = True, jcS: bool = True,
+                        irS: bool = True) -> Tuple[int, int, int]:
+    """Device pointers (0 where not requested); asking for irank may derive it."""
     a, b, c = _P(), _P(), _P()
-    _check(lib().fsparse_plan_arrays(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
-           "fsparse_plan_arrays")
+    _check(lib().fsparse_plan_arrays(plan, ctypes.byref(a) if irank else None,
+                                     ctypes.byref(b) if jcS else None,
+                                     ctypes.byref(c) if irS else None), "fsparse_plan_arrays")
     return a.value or 0, b.value or 0, c.value or 0
 
 
@@ -262,15 +265,15 @@ class Plan:
 
     @property
     def irank(self):
-        return self._view(fsparse_plan_arrays(self.handle)[0], self.len)
+        return self._view(fsparse_plan_arrays(self.handle, True, False, False)[0], self.len)
 
     @property
     def jcS(self):
-        return self._view(fsparse_plan_arrays(self.handle)[1], self.n + 1)
+        return self._view(fsparse_plan_arrays(self.handle, False, True, False)[1], self.n + 1)
 
     @property
     def irS(self):
-        return self._view(fsparse_plan_arrays(self.handle)[2], self.cap)
+        return self._view(fsparse_plan_arrays(self.handle, False, False, True)[2], self.cap)
 
     def numeric(self, s, out=None):
         return numeric(self, s, out)
