@@ -16,14 +16,15 @@
 //                write per triplet, the only global reordering pass;
 //   4. emit:     one CTA per bucket (taken by atomic ticket) loads the bucket,
 //                compresses the row range, sorts (column, row) with a stable
-//                LSD radix sort in shared memory (rank.cuh), puts
-//                each run of equal keys back into ascending k (the scatter
-//                keeps no order inside a block), detects runs by comparing
-//                neighbours (the collision detection of Part 3), numbers the
-//                slots with one decoupled look-back across buckets, and writes
-//                perm, irS, jcS (Part 4's prefix, per bucket column),
-//                and the numeric chunk slot bases (the values are folded by
-//                the numeric kernel afterwards).
+//                LSD radix sort in shared memory (rank.cuh), detects runs by
+//                comparing neighbours (the collision detection of Part 3),
+//                numbers the slots with one decoupled look-back across
+//                buckets, and writes perm -- each run in ascending k, since
+//                the scatter keeps no order inside a block: every triplet
+//                counts the triplets of its run with a smaller k and lands
+//                that far into the run --, irS, jcS (Part 4's prefix, per
+//                bucket column) and the numeric chunk slot bases (the values
+//                are folded by the numeric kernel afterwards).
 //
 // A bucket above the kernel's capacity, or a run longer than kRunSortMax,
 // sets DevStatus::overflow; the host then redoes the call with the global
@@ -38,7 +39,7 @@ namespace fsp {
 
 constexpr int64_t kMaxBuckets = 32768;
 constexpr int kMaxColBits = 12;     // 2^cs column counters in shared memory
-constexpr int kRunSortMax = 128;    // longest run re-sorted by one thread
+constexpr int kRunSortMax = 128;    // longest run put back into k order in the bucket kernel
 constexpr int kRowBits = 1 << 16;   // row ranges up to this are compressed to dense ranks
 
 struct BucketShape {
@@ -271,15 +272,21 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         rbits = bits_of(range ? range - 1 : 0u);
     }
     const int npass = (a.cs + rbits + 7) / 8;
+    // When a row rank replaces the row, the row offset (< 2^16) rides along
+    // in the bits above the sorted digits, so the output needs no search.
+    const int stash_shift = kb + 8 * npass;
+    const bool stash = dense && stash_shift + 16 <= 64;
     // Sort key inside the bucket: (column low bits, row rank), then k below it.
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
         if (valid[i]) {
             const uint64_t w = pk[i];
-            uint32_t row = (uint32_t)((w >> kb) & ((1ull << rb) - 1)) - row_lo;
-            if (dense) row = s_pref[row >> 5] + __popc(s_bits[row >> 5] & ((1u << (row & 31)) - 1u));
+            const uint32_t roff = (uint32_t)((w >> kb) & ((1ull << rb) - 1)) - row_lo;
+            uint32_t row = roff;
+            if (dense) row = s_pref[roff >> 5] + __popc(s_bits[roff >> 5] & ((1u << (roff & 31)) - 1u));
             const uint64_t lowcol = w >> (kb + rb);
             pk[i] = (((lowcol << rbits) | row) << kb) | (w & kmask);
+            if (stash) pk[i] |= (uint64_t)roff << stash_shift;
         }
     }
 
@@ -369,28 +376,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
     }
     __syncthreads();
 
-    // Ascending k inside every run (the scatter kept no order within a block).
-    for (uint32_t h = tid; h < U; h += THREADS) {
-        const int lo = s_hpos[h], hi = s_hpos[h + 1];
-        if (hi - lo > kRunSortMax) {
-            atomicOr(&a.st->overflow, 1u);
-            continue;
-        }
-        for (int p = lo + 1; p < hi; ++p) {
-            const uint64_t v = s_w[p];
-            int q = p - 1;
-            while (q >= lo && s_w[q] > v) {
-                s_w[q + 1] = s_w[q];
-                --q;
-            }
-            s_w[q + 1] = v;
-        }
-    }
-    __syncthreads();
     const uint32_t E = s_misc[3];
 
-    // perm, irS, column counts, chunk slot bases (warp-striped).
+    // perm, irS, column counts, chunk slot bases (warp-striped).  A triplet
+    // of run [lo, hi) goes to lo + (number of triplets of the run with a
+    // smaller k): ascending k inside the run, the head bit on the first.
     const uint64_t rmaskx = (1ull << rbits) - 1;
+    const uint64_t cmask = (1ull << a.cs) - 1;
+    const uint32_t *s_w32 = reinterpret_cast<const uint32_t *>(s_w);   // low words: k and equal key bits
     {
         uint32_t before = wbase;   // heads at earlier positions
         const uint32_t lt = lanemask_lt();
@@ -398,26 +391,44 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         for (int i = 0; i < IPT; ++i) {
             const int p = warp * 32 * IPT + i * 32 + lane;
             const bool head = (hb[i] >> lane) & 1u;
-            const uint32_t slot = E + before + __popc(hb[i] & lt) + (head ? 0u : 0xffffffffu);
+            const uint32_t run = before + __popc(hb[i] & lt) - (head ? 0u : 1u);
             before += __popc(hb[i]);
             if (p >= nx) continue;
+            const uint32_t slot = E + run;
             const uint64_t v = s_w[p];
             const uint32_t k = (uint32_t)(v & kmask);
             const uint64_t sk = v >> kb;
-            const int64_t gp = b0 + p;
-            a.perm[gp] = k | (head ? kHeadBit : 0u);
-            if (head) {
-                uint32_t row = (uint32_t)(sk & rmaskx);
-            if (dense) {   // row of dense rank `row`: word by binary search, bit by __fns
-                int lo = 0, hi = kRowBits / 32 - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pref[mid] <= row) lo = mid; else hi = mid - 1;
+            const int lo = s_hpos[run], hi = s_hpos[run + 1];
+            int dest = p;
+            if (hi - lo > 1) {
+                if (hi - lo > kRunSortMax) {
+                    atomicOr(&a.st->overflow, 1u);   // redone by the onesweep path
+                } else {
+                    const uint32_t kl = (uint32_t)v;
+                    int rank = 0;
+                    for (int q = lo; q < hi; ++q) rank += s_w32[2 * q] < kl;
+                    dest = lo + rank;
                 }
-                row = (uint32_t)lo * 32 + __fns(s_bits[lo], 0, (int)(row - s_pref[lo]) + 1);
             }
-            if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)(row + row_lo);
-                const uint32_t lowcol = (uint32_t)(sk >> rbits);
+            const int64_t gp = b0 + p;
+            a.perm[b0 + dest] = k | (dest == lo ? kHeadBit : 0u);
+            if (head) {
+                uint32_t row;
+                if (stash) {
+                    row = (uint32_t)(v >> stash_shift) & 0xffffu;
+                } else {
+                    row = (uint32_t)(sk & rmaskx);
+                    if (dense) {   // row of dense rank `row`: word by binary search, bit by __fns
+                        int wlo = 0, whi = kRowBits / 32 - 1;
+                        while (wlo < whi) {
+                            const int mid = (wlo + whi + 1) >> 1;
+                            if (s_pref[mid] <= row) wlo = mid; else whi = mid - 1;
+                        }
+                        row = (uint32_t)wlo * 32 + __fns(s_bits[wlo], 0, (int)(row - s_pref[wlo]) + 1);
+                    }
+                }
+                if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)(row + row_lo);
+                const uint32_t lowcol = (uint32_t)((sk >> rbits) & cmask);
                 if (in_range(lowcol, ncols, a.st)) atomicAdd(&s_col[lowcol], 1u);
             }
             if ((gp & (kChunk - 1)) == 0) a.chunk_slot0[gp >> kChunkShift] = head ? slot : slot + 1;
