@@ -11,6 +11,10 @@ rules that the paper leaves to the caller:
 
 * §2.2 (text before the input listing): a zero dimension is implicit, the
   largest index; App. A pre-processing rejects indices below 1.
+* App. A pre-processing of Matlab's double index arrays (``getix``,
+  ``assemble_f64``): a value below 1.0 or different from its ceiling is a
+  bad index.  Reading for values the paper's ``int`` cannot hold: above
+  2^31 - 1 is a bad index too.
 * ``nzmax`` appears only in the call signature of §1.  Reading used here:
   0 means "exactly nnz"; nzmax >= nnz gives that capacity with the unused
   tail zero-filled (irS = 0, prS = +0.0); 0 < nzmax < nnz is an error.
@@ -47,7 +51,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC]
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _SO)
     return _SO
@@ -69,6 +73,8 @@ def _load():
         lib.oracle_numeric.restype = None
         lib.oracle_adjoint.argtypes = [i32p, f64p, ctypes.c_int64, f64p]
         lib.oracle_adjoint.restype = None
+        lib.oracle_getix.argtypes = [f64p, ctypes.c_int64, i32p]
+        lib.oracle_getix.restype = ctypes.c_int64
         lib.oracle_set_mutation.argtypes = [ctypes.c_int]
         lib.oracle_set_mutation.restype = ctypes.c_int
         _lib = lib
@@ -102,6 +108,26 @@ class Result:
     jcS: Optional[np.ndarray] = None     # int32[n+1]
     irS: Optional[np.ndarray] = None     # int32[cap], 0-based rows
     prS: Optional[np.ndarray] = None     # float64[cap] (None for symbolic-only)
+
+
+def getix(ival):
+    """Double index array -> (number of bad values, int32 indices)."""
+    ival = _f64(ival)
+    out = np.empty(max(ival.size, 1), np.int32)
+    bad = _load().oracle_getix(_p(ival, ctypes.c_double), ival.size, _p(out, ctypes.c_int32))
+    return int(bad), out[: ival.size]
+
+
+def assemble_f64(ii, jj, s=None, m: int = 0, n: int = 0, nzmax: int = 0) -> Result:
+    """``sparse(i, j, s, m, n, nzmax)`` with Matlab's double index arrays."""
+    ii, jj = _f64(ii), _f64(jj)
+    if ii.shape != jj.shape:
+        return Result(ERR_ARG)
+    bi, i32 = getix(ii)
+    bj, j32 = getix(jj)
+    if bi or bj:
+        return Result(ERR_INDEX)
+    return assemble(i32, j32, s, m, n, nzmax)
 
 
 def dims(ii, jj, m: int = 0, n: int = 0):

@@ -21,6 +21,10 @@
  *     index; App. A pre-processing rejects any index below 1.
  *   * App. A post-processing: the sum runs over k in ascending order into a
  *     zero-initialised prS, i.e. the fold (((+0.0 + s_a) + s_b) + ...).
+ *   * App. A pre-processing of Matlab's double index arrays (oracle_getix):
+ *     a value below 1.0, or one that differs from its ceiling, is a bad
+ *     index; the rest become int.  Reading for values the paper's int cannot
+ *     hold: above 2^31 - 1 is a bad index too.
  *
  * The method reaches an exactly defined result, so this oracle is that
  * definition written out: sort the tuples (j, i, k) lexicographically with
@@ -32,6 +36,7 @@
  * show that every pin catches a plausible bug in this file.  It is zero by
  * default and nothing outside tests/ sets it.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -56,6 +61,30 @@ int oracle_set_mutation(int m) {
  * dimension must bound its indices; a zero dimension is inferred as the
  * largest index (0 when len == 0).
  */
+/*
+ * App. A pre-processing: Matlab passes index arrays as double.  Each value
+ * must be at least 1.0 and equal to its ceiling (an integer); NaN fails the
+ * second test.  Values above 2^31 - 1 do not fit the paper's int and are bad
+ * as well.  Writes the converted indices to out[len] and returns the number
+ * of bad values (0 = all good; out is then complete).
+ */
+int64_t oracle_getix(const double *ival, int64_t len, int32_t *out) {
+    int64_t bad = 0;
+    for (int64_t k = 0; k < len; k++) {
+        const double x = ival[k];
+        int ok = !(x < 1.0 || x != ceil(x)) && x <= 2147483647.0;
+        if (g_mutation == 10) ok = x >= 1.0 && x <= 2147483647.0;          /* planted: fractions accepted */
+        if (g_mutation == 11) ok = !(x < 0.0 || x != ceil(x)) && x <= 2147483647.0; /* planted: zero accepted */
+        if (!ok) {
+            bad++;
+            out[k] = 0;
+        } else {
+            out[k] = (int32_t)x;
+        }
+    }
+    return bad;
+}
+
 int oracle_dims(const int32_t *ii, const int32_t *jj, int64_t len,
                 int32_t m, int32_t n, int32_t *m_out, int32_t *n_out) {
     if (len < 0 || m < 0 || n < 0) return ORACLE_ERR_ARG;

@@ -263,6 +263,57 @@ def pin_paper_counting_method(seed: int = 13):
         assert r.irS.tolist() == irS and np.array_equal(bits(r.prS), bits(prS))
 
 
+# App. A pre-processing of Matlab's double index arrays: a value below 1.0 or
+# different from its ceiling is a bad index; the reading for values the
+# paper's int cannot hold makes anything above 2^31 - 1 bad too.  Each case
+# is (value, expected int or None for "bad"), written out by hand.
+GETIX_CASES = [
+    (1.0, 1), (2.0, 2), (3.0, 3), (12345.0, 12345), (2147483647.0, 2147483647),
+    (0.0, None), (-0.0, None), (-1.0, None), (0.5, None), (1.5, None), (2.25, None),
+    (np.nextafter(1.0, 2.0), None), (np.nextafter(2.0, 1.0), None), (5e-324, None),
+    (float("nan"), None), (float("inf"), None), (float("-inf"), None),
+    (2147483648.0, None), (1e300, None), (-2147483648.0, None),
+]
+
+
+def getix_rule(x: float):
+    """The pre-processing rule restated with Python's own float predicates."""
+    x = float(x)
+    if np.isfinite(x) and x.is_integer() and 1 <= x <= 2**31 - 1:
+        return int(x)
+    return None
+
+
+def pin_getix(seed: int = 21):
+    vals = np.array([c[0] for c in GETIX_CASES])
+    bad, out = oracle.getix(vals)
+    want = [c[1] for c in GETIX_CASES]
+    assert bad == sum(w is None for w in want), "bad-index count (App. A pre-processing)"
+    for (x, w), o in zip(GETIX_CASES, out.tolist()):
+        if w is not None:
+            assert o == w, f"{x!r} converts to {w}"
+    g = np.random.Generator(np.random.PCG64(seed))
+    ints = g.integers(-5, 1 << 31, 4000).astype(np.float64)
+    near = np.nextafter(ints, ints + g.choice([-1.0, 1.0], ints.size))
+    frac = g.uniform(-3, 3e9, 4000)
+    x = np.concatenate([ints, near, frac, [0.0, 1.0, 2.0**31 - 1, 2.0**31]])
+    bad, out = oracle.getix(x)
+    exp = [getix_rule(v) for v in x]
+    assert bad == sum(e is None for e in exp)
+    for v, e, o in zip(x.tolist(), exp, out.tolist()):
+        if e is not None:
+            assert o == e, f"{v!r} converts to {e}"
+    # the running example given as Matlab doubles yields the printed Eq. (2.1) arrays
+    g = golden()
+    t, e = g["running_example"], g["matrix_eq_2_1"]
+    r = oracle.assemble_f64(np.array(t["ii"], float), np.array(t["jj"], float), t["s"])
+    assert r.status == oracle.OK and r.jcS.tolist() == e["jcS"]
+    assert r.irS.tolist() == e["irS"] and r.prS.tolist() == e["prS"]
+    for k, bad_value in ((4, 1.5), (0, 0.0), (12, float("nan"))):
+        ii = np.array(t["ii"], float)
+        ii[k] = bad_value
+        assert oracle.assemble_f64(ii, np.array(t["jj"], float), t["s"]).status == oracle.ERR_INDEX
+
 ALL_PINS = [
     pin_eq21_from_sorted_input,
     pin_running_example,
@@ -276,4 +327,5 @@ ALL_PINS = [
     pin_nzmax,
     pin_numeric_and_adjoint,
     pin_paper_counting_method,
+    pin_getix,
 ]

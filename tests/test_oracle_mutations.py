@@ -14,6 +14,8 @@ PLANTED = {
     7: "last term of each run dropped",
     8: "only k-adjacent repeats merged",
     9: "run heads point one slot back",
+    10: "non-integer double indices accepted",
+    11: "zero double index accepted",
 }
 
 
