@@ -145,6 +145,27 @@ fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const doub
                                 fsparse_plan *plan_out);
 
 /* ------------------------------------------------------------------------
+ * Matlab-style double index arrays (App. A pre-processing of the index
+ * input): ii and jj are device double[len] holding unit-offset indices, as
+ * Matlab passes them.  Each value must be at least 1.0 and equal to its
+ * ceiling (an integer; NaN fails); this library also rejects values above
+ * 2^31 - 1, which the paper's int cannot hold.  A rejected value gives
+ * FSPARSE_ERR_INDEX and no plan, exactly as an out-of-range int index does.
+ * Otherwise the calls behave as fsparse_symbolic / fsparse_assemble on the
+ * converted indices (same arguments, results, ownership and synchronisation);
+ * the conversion uses 8*len bytes of temporary device memory from the same
+ * stream-ordered pool, handed back to the pool (in stream order) before the
+ * call returns.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_symbolic_f64(const double *ii, const double *jj, int64_t len, int32_t m,
+                                    int32_t n, int64_t nzmax, void *stream, fsparse_plan *plan_out);
+
+fsparse_status fsparse_assemble_f64(const double *ii, const double *jj, const double *sr,
+                                    int64_t len, int32_t m, int32_t n, int64_t nzmax,
+                                    double *prS, int64_t prS_capacity, void *stream,
+                                    fsparse_plan *plan_out);
+
+/* ------------------------------------------------------------------------
  * Batched numeric re-assembly of many independent patterns (many small
  * assemblies per time step).  The batch concatenates `count` plans: triplet
  * k of plan b is element h_len_off[b] + k of the concatenated sr, and slot

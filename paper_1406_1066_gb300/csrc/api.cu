@@ -373,6 +373,61 @@ fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const doub
     return launch_numeric(p->perm, p->chunk_slot0, p->len, p->numeric_tile, sr, prS, p->nnz, p->cap, s);
 }
 
+// ---- Matlab-style double index arrays ----------------------------------------
+// Converted once into int32 scratch (App. A pre-processing), then the int
+// path runs; a bad value becomes index 0, so the int path's own check returns
+// FSPARSE_ERR_INDEX at its usual synchronisation.
+static fsparse_status check_f64_args(const double *ii, const double *jj, int64_t len, int32_t m,
+                                     int32_t n, int64_t nzmax, void *plan_out) {
+    if (!plan_out) return set_error(FSPARSE_ERR_ARG, "plan_out is NULL");
+    if (len < 0) return set_error(FSPARSE_ERR_ARG, "len < 0");
+    if (m < 0 || n < 0) return set_error(FSPARSE_ERR_ARG, "negative dimension");
+    if (nzmax < 0) return set_error(FSPARSE_ERR_ARG, "nzmax < 0");
+    if (len > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "len above 2^30 - 1");
+    if (nzmax > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "nzmax above 2^30 - 1");
+    if (len > 0 && (!ii || !jj)) return set_error(FSPARSE_ERR_ARG, "NULL index array");
+    return FSPARSE_OK;
+}
+
+static fsparse_status getix_pair(const double *ii, const double *jj, int64_t len, Scratch &scratch,
+                                 int32_t **i32, int32_t **j32, cudaStream_t s) {
+    fsparse_status e;
+    int dev = 0;
+    FSP_CUDA(cudaGetDevice(&dev));
+    if ((e = ensure_pool(dev)) != FSPARSE_OK) return e;
+    const size_t n = (size_t)std::max<int64_t>(len, 1);
+    if ((e = scratch.get(i32, n)) != FSPARSE_OK || (e = scratch.get(j32, n)) != FSPARSE_OK) return e;
+    if ((e = launch_getix(ii, len, *i32, s)) != FSPARSE_OK) return e;
+    return launch_getix(jj, len, *j32, s);
+}
+
+fsparse_status fsparse_symbolic_f64(const double *ii, const double *jj, int64_t len, int32_t m,
+                                    int32_t n, int64_t nzmax, void *stream, fsparse_plan *plan_out) {
+    fsparse_status e = check_f64_args(ii, jj, len, m, n, nzmax, plan_out);
+    if (e != FSPARSE_OK) return e;
+    *plan_out = nullptr;
+    cudaStream_t s = as_stream(stream);
+    Scratch scratch(s);
+    int32_t *i32 = nullptr, *j32 = nullptr;
+    if ((e = getix_pair(ii, jj, len, scratch, &i32, &j32, s)) != FSPARSE_OK) return e;
+    return fsparse_symbolic(i32, j32, len, m, n, nzmax, stream, plan_out);
+}
+
+fsparse_status fsparse_assemble_f64(const double *ii, const double *jj, const double *sr, int64_t len,
+                                    int32_t m, int32_t n, int64_t nzmax, double *prS,
+                                    int64_t prS_capacity, void *stream, fsparse_plan *plan_out) {
+    fsparse_status e = check_f64_args(ii, jj, len, m, n, nzmax, plan_out);
+    if (e != FSPARSE_OK) return e;
+    *plan_out = nullptr;
+    if (len > 0 && !sr) return set_error(FSPARSE_ERR_ARG, "NULL value array");
+    if (prS_capacity < 0 || (prS_capacity > 0 && !prS)) return set_error(FSPARSE_ERR_ARG, "bad prS");
+    cudaStream_t s = as_stream(stream);
+    Scratch scratch(s);
+    int32_t *i32 = nullptr, *j32 = nullptr;
+    if ((e = getix_pair(ii, jj, len, scratch, &i32, &j32, s)) != FSPARSE_OK) return e;
+    return fsparse_assemble(i32, j32, sr, len, m, n, nzmax, prS, prS_capacity, stream, plan_out);
+}
+
 // ---- batch ----------------------------------------------------------------
 fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, void *stream,
                                     fsparse_batch *batch_out) {

@@ -234,6 +234,42 @@ fsparse_status launch_fill(int32_t *irS, double *prS, int64_t from, int64_t to, 
     return FSPARSE_OK;
 }
 
+// App. A pre-processing of Matlab's double index arrays: a value below 1.0,
+// not an integer (NaN included), or above 2^31 - 1 -- the reading for values
+// the paper's int cannot hold -- becomes 0, which the symbolic pass then
+// reports as a bad index; every other value becomes its int.
+__device__ __forceinline__ int32_t getix_one(double x) {
+    if (!(x >= 1.0 && x <= 2147483647.0)) return 0;
+    const int32_t v = (int32_t)x;   // truncation: exact for integral x in range
+    return (double)v == x ? v : 0;
+}
+
+__global__ void getix_kernel(const double *__restrict__ ival, int64_t len, int32_t *__restrict__ out,
+                             int vec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n2 = len / 2;
+        for (int64_t v = t0; v < n2; v += stride) {
+            const double2 x = reinterpret_cast<const double2 *>(ival)[v];
+            reinterpret_cast<int2 *>(out)[v] = make_int2(getix_one(x.x), getix_one(x.y));
+        }
+        done = n2 * 2;
+    }
+    for (int64_t k = done + t0; k < len; k += stride) out[k] = getix_one(ival[k]);
+}
+
+fsparse_status launch_getix(const double *ival, int64_t len, int32_t *out, cudaStream_t s) {
+    if (len <= 0) return FSPARSE_OK;
+    const int vec = ((reinterpret_cast<uintptr_t>(ival) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    const int64_t work = vec ? (len + 1) / 2 : len;
+    const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count(0) * 8);
+    getix_kernel<<<std::max(grid, 1), 256, 0, s>>>(ival, len, out, vec);
+    FSP_LAUNCHED();
+    return FSPARSE_OK;
+}
+
 __global__ void iota_kernel(uint32_t *perm, int64_t len) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < len;
          p += (int64_t)gridDim.x * blockDim.x)

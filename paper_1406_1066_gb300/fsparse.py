@@ -71,6 +71,8 @@ def lib() -> ctypes.CDLL:
         "fsparse_numeric": [_P, _P, _P, _P],
         "fsparse_numeric_adjoint": [_P, _P, _P, _P],
         "fsparse_assemble": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
+        "fsparse_symbolic_f64": [_P, _P, _I64, _I32, _I32, _I64, _P, ctypes.POINTER(_P)],
+        "fsparse_assemble_f64": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_batch_create": [_I32, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)],
         "fsparse_batch_info": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
         "fsparse_batch_numeric": [_P, _P, _P, _P],
@@ -149,6 +151,24 @@ def fsparse_assemble(ii: int, jj: int, sr: int, length: int, m: int, n: int, nzm
     if st != OK and out.value:
         lib().fsparse_plan_destroy(out.value)
     _check(st, "fsparse_assemble")
+    return out.value
+
+
+def fsparse_symbolic_f64(ii: int, jj: int, length: int, m: int, n: int, nzmax: int, stream: int) -> int:
+    out = _P()
+    _check(lib().fsparse_symbolic_f64(ii, jj, length, m, n, nzmax, stream, ctypes.byref(out)),
+           "fsparse_symbolic_f64")
+    return out.value
+
+
+def fsparse_assemble_f64(ii: int, jj: int, sr: int, length: int, m: int, n: int, nzmax: int, prS: int,
+                         capacity: int, stream: int) -> int:
+    out = _P()
+    st = lib().fsparse_assemble_f64(ii, jj, sr, length, m, n, nzmax, prS, capacity, stream,
+                                    ctypes.byref(out))
+    if st != OK and out.value:
+        lib().fsparse_plan_destroy(out.value)
+    _check(st, "fsparse_assemble_f64")
     return out.value
 
 
@@ -290,14 +310,25 @@ class Plan:
             pass
 
 
+def _index_dtype(ii, jj):
+    """int32 indices, or float64 ones (Matlab's double arrays, App. A)."""
+    torch = _torch()
+    dt = ii.dtype if isinstance(ii, torch.Tensor) else None
+    if dt not in (torch.int32, torch.float64):
+        raise TypeError(f"ii must be int32 or float64, got {dt}")
+    _dev(ii, dt, "ii")
+    _dev(jj, dt, "jj")
+    return dt == torch.float64
+
+
 def symbolic(ii, jj, m: int = 0, n: int = 0, nzmax: int = 0) -> Plan:
     torch = _torch()
-    _dev(ii, torch.int32, "ii")
-    _dev(jj, torch.int32, "jj")
+    f64 = _index_dtype(ii, jj)
     if ii.numel() != jj.numel():
         raise ValueError("ii and jj differ in length")
+    call = fsparse_symbolic_f64 if f64 else fsparse_symbolic
     with torch.cuda.device(ii.device):
-        h = fsparse_symbolic(ii.data_ptr(), jj.data_ptr(), ii.numel(), m, n, nzmax, _stream())
+        h = call(ii.data_ptr(), jj.data_ptr(), ii.numel(), m, n, nzmax, _stream())
     return Plan(h, ii.device)
 
 
@@ -332,11 +363,12 @@ def numeric_adjoint(plan: Plan, dprS, out=None):
 def assemble(ii, jj, s, m: int = 0, n: int = 0, nzmax: int = 0, prS=None):
     """``S = sparse(i, j, s, m, n, nzmax)`` -> (jcS, irS, prS, plan).
 
-    jcS and irS are views of the plan's arrays; prS has the plan's capacity.
+    ii and jj are int32, or float64 as Matlab passes them (App. A
+    pre-processing: non-integer or < 1 values are bad indices).  jcS and irS
+    are views of the plan's arrays; prS has the plan's capacity.
     """
     torch = _torch()
-    _dev(ii, torch.int32, "ii")
-    _dev(jj, torch.int32, "jj")
+    f64 = _index_dtype(ii, jj)
     _dev(s, torch.float64, "s")
     L = ii.numel()
     if jj.numel() != L or s.numel() != L:
@@ -344,9 +376,10 @@ def assemble(ii, jj, s, m: int = 0, n: int = 0, nzmax: int = 0, prS=None):
     if prS is None:
         prS = torch.empty(max(L, nzmax, 1), dtype=torch.float64, device=ii.device)
     _dev(prS, torch.float64, "prS")
+    call = fsparse_assemble_f64 if f64 else fsparse_assemble
     with torch.cuda.device(ii.device):
-        h = fsparse_assemble(ii.data_ptr(), jj.data_ptr(), s.data_ptr(), L, m, n, nzmax,
-                             prS.data_ptr(), prS.numel(), _stream())
+        h = call(ii.data_ptr(), jj.data_ptr(), s.data_ptr(), L, m, n, nzmax,
+                 prS.data_ptr(), prS.numel(), _stream())
     plan = Plan(h, ii.device)
     return plan.jcS, plan.irS, prS[: plan.cap], plan
 

@@ -76,6 +76,17 @@ def test_argument_errors_without_device(lib):
     assert lib.fsparse_plan_destroy(None) == fsparse.OK
     assert lib.fsparse_batch_destroy(None) == fsparse.OK
     assert lib.fsparse_assemble(None, None, None, 0, 0, 0, 0, None, 0, None, None) == fsparse.ERR_ARG
+    # double-index entry points validate before touching the device
+    for args, status in (((0, 0, -1, 3, 3, 0, 0), fsparse.ERR_ARG), ((0, 0, 10, 3, 3, 0, 0), fsparse.ERR_ARG),
+                         ((8, 8, 2**30, 3, 3, 0, 0), fsparse.ERR_SIZE), ((8, 8, 4, -3, 3, 0, 0), fsparse.ERR_ARG),
+                         ((8, 8, 4, 3, 3, -1, 0), fsparse.ERR_ARG)):
+        with pytest.raises(fsparse.FsparseError) as e:
+            fsparse.fsparse_symbolic_f64(*args)
+        assert e.value.status == status
+    assert lib.fsparse_symbolic_f64(None, None, 0, 0, 0, 0, None, None) == fsparse.ERR_ARG
+    assert lib.fsparse_assemble_f64(None, None, None, 0, 0, 0, 0, None, 0, None, None) == fsparse.ERR_ARG
+    assert lib.fsparse_assemble_f64(8, 8, None, 4, 3, 3, 0, None, 0, None,
+                                    ctypes.byref(fsparse._P())) == fsparse.ERR_ARG   # NULL values
 
 
 def test_config_resolution_is_host_logic(lib):
