@@ -166,6 +166,25 @@ def oracle_job(t, frac_den: int, numeric_steps: int):
     return time.perf_counter() - t0, Ls
 
 
+def paper_method_job(t, frac_den: int):
+    """The paper's own CPU method (serial §2.3, threaded §3) on the same sample: full assembly."""
+    from oracle import paper_method
+    Ls = (t.L // frac_den) // 16 * 16
+    ii, jj, s = t.ii[:Ls].copy(), t.jj[:Ls].copy(), t.s[:Ls].copy()
+    out = {"unit": "G triplets/s (full assembly)", "kind": "paper method (§2.3 serial, §3 threaded)",
+           "openmp": None, "sample": f"first {Ls} triplets (1/{frac_den} of the workload, element order)"}
+    t0 = time.perf_counter()
+    paper_method.assemble(ii, jj, s, t.m, t.n, threads=None, want_irank=False)
+    sec = time.perf_counter() - t0
+    out["serial"] = {"value": Ls / sec / 1e9, "seconds": sec, "cores": 1}
+    t0 = time.perf_counter()
+    _, used = paper_method.assemble(ii, jj, s, t.m, t.n, threads=0, want_irank=False)
+    sec = time.perf_counter() - t0
+    out["threaded"] = {"value": Ls / sec / 1e9, "seconds": sec, "cores": used}
+    out["openmp"] = bool(paper_method.openmp)
+    return out
+
+
 def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -384,6 +403,10 @@ def gpu_arm(args):
                "sample": f"first {Ls} triplets (1/4 of the cube, element order): one oracle assembly "
                          f"+ {NUMERIC_STEPS} oracle numeric passes, single thread"}
 
+    paper_cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        paper_cpu = paper_method_job(t, 4 if t.L > 10**7 else 1)
+
     if rank == 0:
         line = {
             "metric": "G triplets/s (full assembly + 50 numeric re-assemblies)",
@@ -406,6 +429,7 @@ def gpu_arm(args):
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_paper_method": paper_cpu,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

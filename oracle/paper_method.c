@@ -1,0 +1,224 @@
+/*
+ * paper_method.c -- the paper's own CPU method for S = sparse(i,j,s,m,n),
+ * serial and multithreaded, written from its description.
+ *
+ * TEST AND BASELINE INFRASTRUCTURE.  Used by the test suite (a third
+ * cross-check of irank / jcS / irS / prS against the sort-based oracle) and
+ * by the benchmark's CPU leg (the paper's method timed on the host cores).
+ * The GPU library shares no code with it and never calls it.
+ *
+ * Source: S. Engblom and D. Lukarski, "Fast Matlab compatible sparse assembly
+ * on multicore computers" (arXiv:1406.1066).
+ *
+ * Serial (§2.3, Parts 1-4, and the App. A post-processing):
+ *   Part 1  count the triplets of every row and accumulate: row pointers
+ *           that ignore collisions;
+ *   Part 2  place the triplet numbers row by row, in input order (a stable
+ *           counting sort by row): the array rank;
+ *   Part 3  sweep the rows in order; a per-column cache of the last row seen
+ *           (hcol) tells a new (row, col) pair from a repeat; a new pair
+ *           bumps its column's count, and every triplet gets "column count
+ *           minus one" as its column-local slot;
+ *   Part 4  accumulate the column counts into jcS and shift every slot by
+ *           the start of its column: irank;
+ *   post    irS[irank[k]] = ii[k] - 1 and prS[irank[k]] += sr[k] for k
+ *           ascending into zeroed storage.
+ *
+ * Multithreaded (§3): the input is cut into one contiguous slice per thread;
+ * each thread counts its rows privately, and per-row prefix sums over the
+ * threads give every thread its own starting cursor inside each row, so
+ * rank stays stable in k.  Rows are then cut into one contiguous range per
+ * thread; each thread sweeps its rows with a private column cache and private
+ * column counters, producing the permuted map irankP[i] = slot of the
+ * triplet at rank position i.  Per-column prefix sums over the threads turn
+ * the private counters into each thread's offset inside every column, and
+ * the post-processing runs over the same row ranges.  Every slot belongs to
+ * one row and hence to one thread, which visits its triplets in ascending k,
+ * so the sums equal the serial ones bit for bit.
+ *
+ * Compiled with -fopenmp when the compiler supports it; otherwise the
+ * pragmas are ignored and the threaded routine runs on one thread.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of threads the threaded routine can use (1 without OpenMP). */
+int paper_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Serial method.  ii, jj unit-offset int32[len], already validated against
+ * M, N.  Outputs irank[len] (may be NULL), jcS[N+1], irS[>= nnz], prS[>= nnz]
+ * (prS may be NULL when sr is NULL).  Returns nnz, or -1 when memory runs out.
+ */
+int64_t paper_sparse_serial(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
+                            int32_t M, int32_t N, int32_t *irank_out, int32_t *jcS, int32_t *irS,
+                            double *prS) {
+    int64_t *rowptr = (int64_t *)calloc((size_t)M + 2, sizeof(int64_t));
+    int64_t *rank = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+    int32_t *hcol = (int32_t *)calloc((size_t)N + 1, sizeof(int32_t));
+    int64_t *colcnt = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
+    int32_t *irank = irank_out ? irank_out : (int32_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int32_t));
+    if (!rowptr || !rank || !hcol || !colcnt || !irank) {
+        free(rowptr); free(rank); free(hcol); free(colcnt);
+        if (!irank_out) free(irank);
+        return -1;
+    }
+    /* Part 1: rowptr[r + 1] counts row r; running sum gives row starts. */
+    for (int64_t k = 0; k < len; k++) rowptr[ii[k]]++;
+    for (int32_t r = 1; r <= M; r++) rowptr[r] += rowptr[r - 1];
+    /* rowptr[r - 1] is now the start of row r (unit offset). */
+    /* Part 2: stable placement by row, the cursor walking through each row. */
+    for (int64_t k = 0; k < len; k++) rank[rowptr[ii[k] - 1]++] = k;
+    /* rowptr[r - 1] is now the end of row r.  Part 3: row-ordered sweep. */
+    int64_t pos = 0;
+    for (int32_t r = 1; r <= M; r++) {
+        for (; pos < rowptr[r - 1]; pos++) {
+            const int64_t k = rank[pos];
+            const int32_t c = jj[k];
+            if (hcol[c] < r) {          /* first time (r, c) is seen */
+                hcol[c] = r;
+                colcnt[c]++;
+            }
+            irank[k] = (int32_t)(colcnt[c] - 1);
+        }
+    }
+    /* Part 4: column starts, then global slots. */
+    jcS[0] = 0;
+    for (int32_t c = 1; c <= N; c++) jcS[c] = (int32_t)(jcS[c - 1] + colcnt[c]);
+    for (int64_t k = 0; k < len; k++) irank[k] += jcS[jj[k] - 1];
+    const int64_t nnz = jcS[N];
+    /* Post-processing, k ascending into zeroed storage. */
+    for (int64_t p = 0; p < nnz; p++) {
+        irS[p] = 0;
+        if (prS) prS[p] = 0.0;
+    }
+    for (int64_t k = 0; k < len; k++) {
+        irS[irank[k]] = ii[k] - 1;
+        if (prS && sr) prS[irank[k]] += sr[k];
+    }
+    free(rowptr); free(rank); free(hcol); free(colcnt);
+    if (!irank_out) free(irank);
+    return nnz;
+}
+
+/*
+ * Multithreaded method on `nthreads` threads (<= 0: all available).  Same
+ * arguments and results as paper_sparse_serial; irank_out, when not NULL,
+ * receives irank[k] = irankP[i] for k = rank[i].  *threads_used (may be
+ * NULL) receives the thread count actually used.
+ */
+int64_t paper_sparse_omp(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
+                         int32_t M, int32_t N, int nthreads, int32_t *irank_out, int32_t *jcS,
+                         int32_t *irS, double *prS, int *threads_used) {
+    int T = nthreads > 0 ? nthreads : paper_max_threads();
+#ifndef _OPENMP
+    T = 1;
+#endif
+    if (threads_used) *threads_used = T;
+    /* rowcur[t][r]: thread t's cursor in row r (unit offset r = 1..M). */
+    int64_t *rowcur = (int64_t *)calloc((size_t)T * ((size_t)M + 1), sizeof(int64_t));
+    int64_t *rowend = (int64_t *)calloc((size_t)M + 1, sizeof(int64_t));   /* end of row r */
+    int64_t *colcnt = (int64_t *)calloc((size_t)T * ((size_t)N + 1), sizeof(int64_t));
+    int64_t *rank = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+    int32_t *irankP = (int32_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int32_t));
+    int32_t *hcol_all = (int32_t *)calloc((size_t)T * ((size_t)N + 1), sizeof(int32_t));
+    if (!rowcur || !rowend || !colcnt || !rank || !irankP || !hcol_all) {
+        free(rowcur); free(rowend); free(colcnt); free(rank); free(irankP); free(hcol_all);
+        return -1;
+    }
+    int64_t nnz = 0;
+#pragma omp parallel num_threads(T)
+    {
+#ifdef _OPENMP
+        const int t = omp_get_thread_num();
+#else
+        const int t = 0;
+#endif
+        int64_t *mycur = rowcur + (size_t)t * ((size_t)M + 1);
+        const int64_t k0 = len * t / T, k1 = len * (t + 1) / T;
+        /* Part 1: private row counts over this thread's input slice. */
+        for (int64_t k = k0; k < k1; k++) mycur[ii[k]]++;
+#pragma omp barrier
+        /* Per row: start of the row, then each thread's cursor after the
+           threads before it (thread order = input order: stable). */
+#pragma omp single
+        {
+            int64_t run = 0;
+            for (int32_t r = 1; r <= M; r++) {
+                for (int u = 0; u < T; u++) {
+                    int64_t *c = rowcur + (size_t)u * ((size_t)M + 1) + r;
+                    const int64_t cnt = *c;
+                    *c = run;
+                    run += cnt;
+                }
+                rowend[r] = run;
+            }
+        }
+        /* Part 2: place this slice's triplets. */
+        for (int64_t k = k0; k < k1; k++) rank[mycur[ii[k]]++] = k;
+#pragma omp barrier
+        /* Part 3: this thread's contiguous row range, private cache/counters. */
+        const int32_t r0 = (int32_t)(1 + (int64_t)M * t / T), r1 = (int32_t)((int64_t)M * (t + 1) / T);
+        int32_t *hcol = hcol_all + (size_t)t * ((size_t)N + 1);
+        int64_t *mycol = colcnt + (size_t)t * ((size_t)N + 1);
+        const int64_t i0 = r0 > 1 ? rowend[r0 - 1] : 0;
+        const int64_t i1 = r1 >= 1 ? rowend[r1] : 0;
+        {
+            int64_t i = i0;
+            for (int32_t r = r0; r <= r1; r++) {
+                for (; i < rowend[r]; i++) {
+                    const int32_t c = jj[rank[i]];
+                    if (hcol[c] < r) {
+                        hcol[c] = r;
+                        mycol[c]++;
+                    }
+                    irankP[i] = (int32_t)(mycol[c] - 1);
+                }
+            }
+        }
+#pragma omp barrier
+        /* Part 4: per column, thread u's slots follow those of threads < u
+           (their rows are smaller); jcS from the totals. */
+#pragma omp single
+        {
+            int64_t run = 0;
+            jcS[0] = 0;
+            for (int32_t c = 1; c <= N; c++) {
+                for (int u = 0; u < T; u++) {
+                    int64_t *p = colcnt + (size_t)u * ((size_t)N + 1) + c;
+                    const int64_t cnt = *p;
+                    *p = run;
+                    run += cnt;
+                }
+                jcS[c] = (int32_t)run;
+            }
+            nnz = run;
+        }
+        for (int64_t i = i0; i < i1; i++) irankP[i] += (int32_t)mycol[jj[rank[i]]];
+        /* Post-processing over the same rows: each slot's triplets are in
+           one row, visited in ascending k. */
+        for (int64_t i = i0; i < i1; i++) {
+            irS[irankP[i]] = 0;
+            if (prS) prS[irankP[i]] = 0.0;
+        }
+        for (int64_t i = i0; i < i1; i++) {
+            const int64_t k = rank[i];
+            irS[irankP[i]] = ii[k] - 1;
+            if (prS && sr) prS[irankP[i]] += sr[k];
+        }
+        if (irank_out)
+            for (int64_t i = i0; i < i1; i++) irank_out[rank[i]] = irankP[i];
+    }
+    free(rowcur); free(rowend); free(colcnt); free(rank); free(irankP); free(hcol_all);
+    return nnz;
+}
