@@ -216,6 +216,30 @@ def reference_arm(args):
 
 
 # --------------------------------------------------------------------------- GPU arm
+def append_timing(torch, fsparse, ii_d, jj_d, t, full_ms, reps: int = 5):
+    """Delayed assembly: the second half of the workload appended to a plan of
+    the first half, against one full symbolic assembly of everything."""
+    half = t.L // 2
+    base = fsparse.symbolic(ii_d[:half], jj_d[:half], t.m, t.n)
+    ms = []
+    for r in range(reps + 2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p2 = fsparse.append(base, ii_d[half:], jj_d[half:])
+        e1.record()
+        torch.cuda.synchronize()
+        if r >= 2:
+            ms.append(e0.elapsed_time(e1))
+        p2.close()
+    base.close()
+    a_ms = statistics.median(ms)
+    return {"ms": a_ms, "appended_triplets": t.L - half, "plan_triplets": half,
+            "gtps_appended": (t.L - half) / a_ms / 1e6, "full_assembly_ms": full_ms,
+            "note": "second half appended to a plan of the first half (symbolic of the new half "
+                    "+ merge); full_assembly_ms assembles all triplets from scratch"}
+
+
 def batched_vs_plain(torch, fsparse, to_dev, steps: int = 100):
     """256 uneven mesh instances: 100 graph-replayed batched steps vs per-plan launches."""
     b = inputs.batch(256, 1416)
@@ -394,6 +418,8 @@ def gpu_arm(args):
     extra = {}
     if rank == 0 and world == 1 and not args.no_batch:
         extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev)
+    if rank == 0 and world == 1:
+        extra["append"] = append_timing(torch, fsparse, ii_d, jj_d, t, full_ms)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -104,6 +104,19 @@ fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank,
 
 /* Release a plan (NULL is a no-op).  Waits for outstanding device work that
    may still read the plan's arrays. */
+/* Delayed assembly (§2 names input that is not all available at the first
+   call as an extension of the method): a NEW plan for the concatenation of
+   the plan's triplets and (ii, jj), device int32[len] unit-offset, whose
+   triplet numbers continue at the plan's len.  The result equals
+   fsparse_symbolic on the concatenated arrays with the plan's m and n: the
+   appended indices must lie within them (FSPARSE_ERR_INDEX otherwise, no
+   plan).  Values for fsparse_numeric on the new plan are the old values
+   followed by the new ones.  The new plan's capacity is its nnz (the old
+   plan's nzmax tail is not carried over).  The old plan is not modified and
+   stays valid; the caller destroys both.  Synchronises `stream`. */
+fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const int32_t *jj,
+                                   int64_t len, void *stream, fsparse_plan *plan_out);
+
 fsparse_status fsparse_plan_destroy(fsparse_plan plan);
 
 /* ------------------------------------------------------------------------

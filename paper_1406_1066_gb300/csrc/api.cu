@@ -428,6 +428,77 @@ fsparse_status fsparse_assemble_f64(const double *ii, const double *jj, const do
     return fsparse_assemble(i32, j32, sr, len, m, n, nzmax, prS, prS_capacity, stream, plan_out);
 }
 
+// ---- delayed assembly ---------------------------------------------------------
+fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const int32_t *jj, int64_t len,
+                                   void *stream, fsparse_plan *plan_out) {
+    if (!plan_out) return set_error(FSPARSE_ERR_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
+    if (len < 0) return set_error(FSPARSE_ERR_ARG, "len < 0");
+    if (len > 0 && (!ii || !jj)) return set_error(FSPARSE_ERR_ARG, "NULL index array");
+    const Plan &a = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    if (a.len + len > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "appended len above 2^30 - 1");
+    if (a.m == 0 || a.n == 0) {
+        if (len > 0) return set_error(FSPARSE_ERR_INDEX, "the plan has a zero dimension");
+    }
+    cudaStream_t s = as_stream(stream);
+    int cur = 0;
+    FSP_CUDA(cudaGetDevice(&cur));
+    if (cur != a.device) return set_error(FSPARSE_ERR_ARG, "the plan belongs to another device");
+
+    // The new triplets alone, checked against the plan's dimensions.
+    Plan *b = nullptr;
+    fsparse_status e = symbolic_impl(ii, jj, nullptr, nullptr, len, a.m, a.n, 0, s, &b, nullptr);
+    if (e != FSPARSE_OK) return e;
+
+    Plan *out = new (std::nothrow) Plan();
+    if (!out) {
+        free_plan_arrays(*b);
+        delete b;
+        return set_error(FSPARSE_ERR_NOMEM, "host allocation");
+    }
+    auto fail = [&](fsparse_status st) {
+        free_plan_arrays(*b);
+        delete b;
+        free_plan_arrays(*out);
+        delete out;
+        return st;
+    };
+    out->device = a.device;
+    out->m = a.m;
+    out->n = a.n;
+    out->len = a.len + len;
+    out->key = a.key;
+    out->cfg = a.cfg;
+    out->numeric_tile = a.numeric_tile;
+    out->nchunks = (out->len + kChunk - 1) / kChunk;
+    const int64_t irs = std::max<int64_t>(a.nnz + b->nnz, 1);
+    if ((e = device_alloc(reinterpret_cast<void **>(&out->irank), (size_t)std::max<int64_t>(out->len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&out->perm), (size_t)std::max<int64_t>(out->len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&out->irS), (size_t)irs * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&out->jcS), ((size_t)out->n + 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&out->chunk_slot0), ((size_t)out->nchunks + 1) * 4, s)))
+        return fail(e);
+    DevStatus h_st{};
+    {
+        Scratch scratch(s);
+        DevStatus *d_st = nullptr;
+        if ((e = scratch.get(&d_st, 1)) != FSPARSE_OK) return fail(e);
+        if (cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+        if ((e = append_merge(a, *b, *out, d_st, scratch, s)) != FSPARSE_OK) return fail(e);
+        if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
+    }
+    if (h_st.timeout) return fail(set_error(FSPARSE_ERR_TIMEOUT, "device look-back wait expired"));
+    if (h_st.oob) return fail(set_error(FSPARSE_ERR_INTERNAL, "internal index check failed"));
+    out->nnz = out->len ? (int64_t)h_st.nnz : 0;
+    out->cap = out->nnz;
+    free_plan_arrays(*b);
+    delete b;
+    *plan_out = reinterpret_cast<fsparse_plan>(out);
+    return FSPARSE_OK;
+}
+
 // ---- batch ----------------------------------------------------------------
 fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, void *stream,
                                     fsparse_batch *batch_out) {

@@ -147,6 +147,9 @@ fsparse_status launch_irank(const uint32_t *perm, const uint32_t *chunk_slot0, i
 fsparse_status launch_fill(int32_t *irS, double *prS, int64_t from, int64_t to, cudaStream_t s);
 fsparse_status launch_iota(uint32_t *perm, int64_t len, cudaStream_t s);
 fsparse_status launch_getix(const double *ival, int64_t len, int32_t *out, cudaStream_t s);
+// Delayed assembly: merge plan a with the plan b of appended triplets into out.
+fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *st, Scratch &scratch,
+                            cudaStream_t s);
 fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t len,
                                    uint32_t offset, cudaStream_t s);
 fsparse_status launch_chunk_heads(const uint32_t *perm, int64_t len, uint32_t *counts,

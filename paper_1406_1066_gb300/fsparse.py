@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
         "fsparse_numeric_adjoint": [_P, _P, _P, _P],
         "fsparse_assemble": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_symbolic_f64": [_P, _P, _I64, _I32, _I32, _I64, _P, ctypes.POINTER(_P)],
+        "fsparse_plan_append": [_P, _P, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_assemble_f64": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_batch_create": [_I32, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)],
         "fsparse_batch_info": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
@@ -151,6 +152,13 @@ def fsparse_assemble(ii: int, jj: int, sr: int, length: int, m: int, n: int, nzm
     if st != OK and out.value:
         lib().fsparse_plan_destroy(out.value)
     _check(st, "fsparse_assemble")
+    return out.value
+
+
+def fsparse_plan_append(plan: int, ii: int, jj: int, length: int, stream: int) -> int:
+    out = _P()
+    _check(lib().fsparse_plan_append(plan, ii, jj, length, stream, ctypes.byref(out)),
+           "fsparse_plan_append")
     return out.value
 
 
@@ -330,6 +338,18 @@ def symbolic(ii, jj, m: int = 0, n: int = 0, nzmax: int = 0) -> Plan:
     with torch.cuda.device(ii.device):
         h = call(ii.data_ptr(), jj.data_ptr(), ii.numel(), m, n, nzmax, _stream())
     return Plan(h, ii.device)
+
+
+def append(plan: Plan, ii, jj) -> Plan:
+    """Delayed assembly: a new plan for the plan's triplets followed by (ii, jj)."""
+    torch = _torch()
+    _dev(ii, torch.int32, "ii")
+    _dev(jj, torch.int32, "jj")
+    if ii.numel() != jj.numel():
+        raise ValueError("ii and jj differ in length")
+    with torch.cuda.device(plan.device):
+        h = fsparse_plan_append(plan.handle, ii.data_ptr(), jj.data_ptr(), ii.numel(), _stream())
+    return Plan(h, plan.device)
 
 
 def numeric(plan: Plan, s, out=None):

@@ -85,6 +85,8 @@ def test_argument_errors_without_device(lib):
         assert e.value.status == status
     assert lib.fsparse_symbolic_f64(None, None, 0, 0, 0, 0, None, None) == fsparse.ERR_ARG
     assert lib.fsparse_assemble_f64(None, None, None, 0, 0, 0, 0, None, 0, None, None) == fsparse.ERR_ARG
+    assert lib.fsparse_plan_append(None, None, None, 0, None, None) == fsparse.ERR_ARG
+    assert lib.fsparse_plan_append(None, None, None, 0, None, ctypes.byref(fsparse._P())) == fsparse.ERR_ARG
     assert lib.fsparse_assemble_f64(8, 8, None, 4, 3, 3, 0, None, 0, None,
                                     ctypes.byref(fsparse._P())) == fsparse.ERR_ARG   # NULL values
 
