@@ -160,8 +160,13 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
                                    DevStatus *d_st, Scratch &scratch, cudaStream_t s, bool *folded) {
     *folded = false;
     fsparse_status e;
+    bool unfit = true;
     if (cfg.strategy == FSPARSE_SORT_BUCKET && bucket_supported(len, plan.n, plan.key, cfg)) {
-        e = bucket_symbolic(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s);
+        e = bucket_symbolic(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s, &unfit);
+        if (e != FSPARSE_OK) return e;
+    }
+    if (!unfit) {
+        e = FSPARSE_OK;
     } else {
         if ((e = onesweep_sort(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan.perm, d_st, scratch, s)) != FSPARSE_OK)
             return e;

@@ -7,10 +7,10 @@
 // triplet numbers continuing at len1.  Both plans are already sorted by
 // (column, row) with runs in ascending k, so the new plan is a merge:
 //
-//   * slot keys: key(s) = column << 32 | row for every CCS slot of each plan
-//     (the column by binary search in jcS);
-//   * ranks: for every slot of one plan, the number of keys of the other plan
-//     below it and whether the other plan holds the same key;
+//   * slot keys: key(s) = column << 32 | row for every CCS slot of each plan;
+//   * ranks by a merge path over the two sorted key lists: for every slot of
+//     one plan, the number of keys of the other plan below it and whether the
+//     other plan holds the same key;
 //   * merged slot of an old slot a = a + (new keys below it) - (shared keys
 //     before it); of a new slot b = b + (old keys below it) - (shared keys
 //     before it); a shared key is one slot;
@@ -40,34 +40,50 @@ __global__ void run_starts_kernel(const uint32_t *__restrict__ perm, const uint3
     }
 }
 
-// key(s) = column << 32 | row: the column is the last c with jcS[c] <= s.
+// key(s) = column << 32 | row, one thread per column writing its slots.
 __global__ void slot_keys_kernel(const int32_t *__restrict__ jcS, int32_t n, const int32_t *__restrict__ irS,
-                                 int64_t nnz, uint64_t *__restrict__ keys) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n - 1;   // jcS[0] = 0 <= s
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((int64_t)jcS[mid] <= s) lo = mid; else hi = mid - 1;
-        }
-        keys[s] = ((uint64_t)(uint32_t)lo << 32) | (uint32_t)irS[s];
+                                 uint64_t *__restrict__ keys) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s0 = jcS[c], s1 = jcS[c + 1];
+        for (int32_t s = s0; s < s1; ++s) keys[s] = ((uint64_t)(uint32_t)c << 32) | (uint32_t)irS[s];
     }
 }
 
-// For every key of `a`: lb = number of keys of `b` below it, eq = 1 when `b`
-// holds the same key.
-__global__ void merge_rank_kernel(const uint64_t *__restrict__ a, int64_t na, const uint64_t *__restrict__ b,
-                                  int64_t nb, uint32_t *__restrict__ lb, uint32_t *__restrict__ eq) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < na;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = a[i];
-        int64_t lo = 0, hi = nb;
-        while (lo < hi) {
+// Merge path over the two sorted key lists (old keys first on ties): thread t
+// finds where merged position 8t falls by one binary search, then merges 8
+// steps.  An old key met at merged position i + j (i old, j new before it)
+// has lbA = j new keys below it; a new key has i old keys not above it, eqB
+// telling whether the last of them is equal, and lbB = i - eqB.
+constexpr int kMergeSteps = 8;
+
+__global__ void merge_path_kernel(const uint64_t *__restrict__ a, int64_t na, const uint64_t *__restrict__ b,
+                                  int64_t nb, uint32_t *__restrict__ lbA, uint32_t *__restrict__ eqA,
+                                  uint32_t *__restrict__ lbB, uint32_t *__restrict__ eqB) {
+    const int64_t total = na + nb;
+    const int64_t nthreads = (total + kMergeSteps - 1) / kMergeSteps;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = t * kMergeSteps;
+        int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+        while (lo < hi) {   // i = old keys among the first d merged
             const int64_t mid = (lo + hi) >> 1;
-            if (b[mid] < x) lo = mid + 1; else hi = mid;
+            if (a[mid] <= b[d - mid - 1]) lo = mid + 1; else hi = mid;
         }
-        lb[i] = (uint32_t)lo;
-        eq[i] = (lo < nb && b[lo] == x) ? 1u : 0u;
+        int64_t i = lo, j = d - lo;
+        const int64_t end = min64(d + kMergeSteps, total);
+        for (int64_t step = d; step < end; ++step) {
+            if (j >= nb || (i < na && a[i] <= b[j])) {
+                lbA[i] = (uint32_t)j;
+                eqA[i] = (j < nb && b[j] == a[i]) ? 1u : 0u;
+                ++i;
+            } else {
+                const uint32_t e = (i > 0 && a[i - 1] == b[j]) ? 1u : 0u;
+                lbB[j] = (uint32_t)(i - e);
+                eqB[j] = e;
+                ++j;
+            }
+        }
     }
 }
 
@@ -156,19 +172,16 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
         FSP_CUDA(cudaMemsetAsync(rsB, 0, 4, s));
     }
     if (na > 0) {
-        slot_keys_kernel<<<grid_for(na), 256, 0, s>>>(a.jcS, a.n, a.irS, na, keyA);
+        slot_keys_kernel<<<grid_for(a.n), 256, 0, s>>>(a.jcS, a.n, a.irS, keyA);
         FSP_LAUNCHED();
     }
     if (nb > 0) {
-        slot_keys_kernel<<<grid_for(nb), 256, 0, s>>>(b.jcS, b.n, b.irS, nb, keyB);
+        slot_keys_kernel<<<grid_for(b.n), 256, 0, s>>>(b.jcS, b.n, b.irS, keyB);
         FSP_LAUNCHED();
     }
-    if (na > 0) {
-        merge_rank_kernel<<<grid_for(na), 256, 0, s>>>(keyA, na, keyB, nb, lbA, eqA);
-        FSP_LAUNCHED();
-    }
-    if (nb > 0) {
-        merge_rank_kernel<<<grid_for(nb), 256, 0, s>>>(keyB, nb, keyA, na, lbB, eqB);
+    if (na + nb > 0) {
+        merge_path_kernel<<<grid_for((na + nb + kMergeSteps - 1) / kMergeSteps), 256, 0, s>>>(
+            keyA, na, keyB, nb, lbA, eqA, lbB, eqB);
         FSP_LAUNCHED();
     }
     if ((e = exclusive_scan_u32(eqA, shA, na, st, scratch, s)) != FSPARSE_OK) return e;

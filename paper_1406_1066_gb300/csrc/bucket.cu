@@ -47,10 +47,12 @@ struct BucketShape {
     int64_t nb = 0;    // number of buckets
     int kb = 1;        // bits of k in a packed word
     int grid = 1;      // blocks of the count/scatter kernels
-    int variant = 0;   // 0: 256 threads x 16 (4096 items), 1: 512 x 16 (8192 items)
 };
 
-static int shape_variant(int target) { return target <= 3000 ? 0 : 1; }
+// Bucket kernel shapes, smallest capacity first; the one used is the
+// smallest whose capacity holds the largest bucket.
+constexpr int kEmitCap[3] = {256 * 16, 512 * 12, 512 * 16};
+constexpr int kMaxBucketCap = 512 * 16;
 
 static bool bucket_shape(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg,
                          BucketShape *out) {
@@ -66,7 +68,6 @@ static bool bucket_shape(int64_t len, int32_t n, const KeyLayout &key, const fsp
     }
     if (sh.nb > kMaxBuckets || sh.cs > kMaxColBits) return false;
     if (sh.cs + key.rb + sh.kb > 64) return false;
-    sh.variant = shape_variant(cfg.bucket_target);
     if (out) *out = sh;
     return true;
 }
@@ -103,6 +104,15 @@ __global__ void bucket_colprefix_kernel(const uint32_t *__restrict__ hist, uint3
         run += v;
     }
     tot[b] = run;
+}
+
+// 2b. largest bucket (atomicMax into *out, zeroed by the caller).
+__global__ void bucket_max_kernel(const uint32_t *__restrict__ tot, int nb, uint32_t *out) {
+    uint32_t m = 0;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) m = max(m, tot[b]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
 // 3. scatter packed words into the buckets (order inside a block's range is
@@ -478,33 +488,62 @@ static fsparse_status run_emit(const BucketEmitArgs &a, int64_t nb, cudaStream_t
 fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
                                int32_t n, const KeyLayout &key,
                                const fsparse_config &cfg, Plan &plan, DevStatus *st, Scratch &scratch,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool *unfit) {
+    *unfit = false;
     BucketShape sh;
-    if (!bucket_shape(len, n, key, cfg, &sh)) return set_error(FSPARSE_ERR_ARG, "bucket path does not fit");
-    const int nb = (int)sh.nb;
-    const size_t table = (size_t)nb * 4;
-    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (200u << 10) / std::max<size_t>(table, 1)));
-    int G = sm_count(0) * per_sm;
-    G = (int)std::max<int64_t>(1, std::min<int64_t>(G, (len + 4095) / 4096));
-    sh.grid = G;
-
-    uint32_t *hist, *goff, *tot, *bstart, *look, *ticket;
+    if (!bucket_shape(len, n, key, cfg, &sh)) {
+        *unfit = true;
+        return FSPARSE_OK;
+    }
+    // Buckets are sized from the average triplets per column; where columns
+    // are filled unevenly (half of them empty, say) the largest bucket can
+    // outgrow shared memory.  The bucket totals are read back once, before
+    // the scatter, and the buckets narrowed until the largest fits.
+    uint32_t *hist = nullptr, *goff = nullptr, *tot = nullptr, *bstart = nullptr, *look, *ticket, *dmax;
     uint64_t *words;
     fsparse_status e;
-    if ((e = scratch.get(&hist, (size_t)nb * G)) || (e = scratch.get(&goff, (size_t)nb * G)) ||
-        (e = scratch.get(&tot, (size_t)nb)) || (e = scratch.get(&bstart, (size_t)nb + 1)) ||
-        (e = scratch.get(&look, (size_t)nb + 1)) || (e = scratch.get(&ticket, 1)) ||
-        (e = scratch.get(&words, (size_t)len)))
+    if ((e = scratch.get(&look, (size_t)kMaxBuckets + 1)) || (e = scratch.get(&ticket, 1)) ||
+        (e = scratch.get(&dmax, 1)) || (e = scratch.get(&tot, (size_t)kMaxBuckets)) ||
+        (e = scratch.get(&bstart, (size_t)kMaxBuckets + 1)) || (e = scratch.get(&words, (size_t)len)))
         return e;
+    int G = 1, nb = 0;
+    uint32_t largest = 0;
+    for (int attempt = 0;; ++attempt) {
+        nb = (int)sh.nb;
+        const size_t table = (size_t)nb * 4;
+        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (200u << 10) / std::max<size_t>(table, 1)));
+        G = sm_count(0) * per_sm;
+        G = (int)std::max<int64_t>(1, std::min<int64_t>(G, (len + 4095) / 4096));
+        if ((e = scratch.get(&hist, (size_t)nb * G)) || (e = scratch.get(&goff, (size_t)nb * G))) return e;
+        FSP_CUDA(cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
+        bucket_count_kernel<<<G, 1024, table, s>>>(jj, len, n, sh.cs, nb, hist, st);
+        FSP_LAUNCHED();
+        bucket_colprefix_kernel<<<(nb + 255) / 256, 256, 0, s>>>(hist, goff, tot, nb, G);
+        FSP_LAUNCHED();
+        FSP_CUDA(cudaMemsetAsync(dmax, 0, 4, s));
+        bucket_max_kernel<<<std::min((nb + 255) / 256, 4 * sm_count(0)), 256, 0, s>>>(tot, nb, dmax);
+        FSP_LAUNCHED();
+        FSP_CUDA(cudaMemcpyAsync(&largest, dmax, 4, cudaMemcpyDeviceToHost, s));
+        FSP_CUDA(cudaStreamSynchronize(s));
+        if (largest <= (uint32_t)kMaxBucketCap) break;
+        if (sh.cs == 0 || attempt >= 3) {   // a column (or a few) beyond the cap: onesweep instead
+            *unfit = true;
+            return FSPARSE_OK;
+        }
+        int shrink = 1;
+        while (shrink < sh.cs && ((uint64_t)kMaxBucketCap << shrink) < largest) ++shrink;
+        sh.cs -= shrink;
+        sh.nb = ((int64_t)(n - 1) >> sh.cs) + 1;
+        if (sh.nb > kMaxBuckets) {
+            *unfit = true;
+            return FSPARSE_OK;
+        }
+    }
+    sh.grid = G;
     FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)nb + 1) * 4, s));
     FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
-
-    FSP_CUDA(cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
-    bucket_count_kernel<<<G, 1024, table, s>>>(jj, len, n, sh.cs, nb, hist, st);
-    FSP_LAUNCHED();
-    bucket_colprefix_kernel<<<(nb + 255) / 256, 256, 0, s>>>(hist, goff, tot, nb, G);
-    FSP_LAUNCHED();
     if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
+    const size_t table = (size_t)nb * 4;
     FSP_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
     bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
                                                  words, st);
@@ -527,7 +566,8 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     a.look = look;
     a.ticket = ticket;
     a.st = st;
-    if (sh.variant == 0) return run_emit<256, 16>(a, nb, s);
+    if (largest <= (uint32_t)kEmitCap[0]) return run_emit<256, 16>(a, nb, s);
+    if (largest <= (uint32_t)kEmitCap[1]) return run_emit<512, 12>(a, nb, s);
     return run_emit<512, 16>(a, nb, s);
 }
 

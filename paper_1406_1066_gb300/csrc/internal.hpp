@@ -155,11 +155,15 @@ fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t l
 fsparse_status launch_chunk_heads(const uint32_t *perm, int64_t len, uint32_t *counts,
                                   int64_t nchunks, cudaStream_t s);
 
-// Hybrid column-bucket path.  Returns FSPARSE_OK and sets *overflow when a
-// bucket does not fit; the caller then redoes the call with onesweep.
+// Hybrid column-bucket path.  Synchronises once to read the largest bucket
+// and narrows the buckets until it fits shared memory; sets *unfit (and does
+// nothing else) when no width fits, so the caller takes the onesweep path.
+// A run longer than the in-bucket limit sets DevStatus::overflow instead,
+// and the caller redoes the call with onesweep.
 fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
                                int32_t n, const KeyLayout &key, const fsparse_config &cfg,
-                               Plan &plan, DevStatus *st, Scratch &scratch, cudaStream_t s);
+                               Plan &plan, DevStatus *st, Scratch &scratch, cudaStream_t s,
+                               bool *unfit);
 bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg);
 
 }  // namespace fsp
