@@ -34,7 +34,7 @@
  *     bits); larger -> FSPARSE_ERR_SIZE.
  *   * Errors never abort, trap or assert on the device.  Device-side
  *     findings (bad index, bounded wait expired) are written to a status
- *     word that the host reads at the single synchronisation point of the
+ *     word that the host reads at the final synchronisation of the
  *     symbolic phase.  On error no plan is returned (*plan_out = NULL)
  *     unless stated otherwise, and output arrays hold unspecified values.
  *   * Entry points are thread-safe with respect to distinct plans.  Calls
@@ -81,8 +81,10 @@ typedef struct fsparse_batch_s *fsparse_batch;
  *            names nzmax only in the call of §1; this is the reading used.)
  *   plan_out receives a new plan on success.
  *
- * Synchronises `stream` once (to read nnz and the device status word).
- * Allocates the plan's device arrays stream-ordered on `stream`.
+ * Synchronises `stream` to read nnz and the device status word; the column
+ * bucket path also reads its largest bucket once before sorting, and implicit
+ * dimensions add one read of the largest indices.  Allocates the plan's
+ * device arrays stream-ordered on `stream`.
  * ---------------------------------------------------------------------- */
 fsparse_status fsparse_symbolic(const int32_t *ii, const int32_t *jj, int64_t len,
                                 int32_t m, int32_t n, int64_t nzmax,
@@ -150,7 +152,7 @@ fsparse_status fsparse_numeric_adjoint(fsparse_plan plan, const double *dprS, do
  * symbolic pass; otherwise the numeric pass runs after nnz is known, and a
  * capacity below the plan's cap returns FSPARSE_ERR_NZMAX WITH the plan
  * (*plan_out set), so the caller can allocate and call fsparse_numeric.
- * plan_out must not be NULL.  Synchronises `stream` once or twice.
+ * plan_out must not be NULL.  Synchronises `stream` as fsparse_symbolic does.
  * ---------------------------------------------------------------------- */
 fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const double *sr,
                                 int64_t len, int32_t m, int32_t n, int64_t nzmax,
