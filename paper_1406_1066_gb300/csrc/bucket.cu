@@ -117,7 +117,7 @@ __global__ void bucket_max_kernel(const uint32_t *__restrict__ tot, int nb, uint
 
 // 3. scatter packed words into the buckets (order inside a block's range is
 //    not kept; the emit kernel restores ascending k inside each run).
-__global__ void bucket_scatter_kernel(const int32_t *__restrict__ ii, const int32_t *__restrict__ jj,
+__global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *__restrict__ ii, const int32_t *__restrict__ jj,
                                       int64_t len, int32_t m, int32_t n, int rb, int cs, int kb,
                                       int nb, const uint32_t *__restrict__ goff,
                                       const uint32_t *__restrict__ bstart, uint64_t *__restrict__ words,
@@ -129,12 +129,26 @@ __global__ void bucket_scatter_kernel(const int32_t *__restrict__ ii, const int3
     __syncthreads();
     const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
     const uint64_t lowmask = (1ull << cs) - 1;
-    for (int64_t k = c0 + tid; k < c1; k += blockDim.x) {
-        const uint32_t i0 = (uint32_t)(checked_index(ii[k], m, st) - 1);
-        const uint32_t j0 = (uint32_t)(checked_index(jj[k], n, st) - 1);
-        const uint32_t pos = atomicAdd(&s_cur[j0 >> cs], 1u);
-        const uint64_t w = ((uint64_t)(j0 & lowmask) << (rb + kb)) | ((uint64_t)i0 << kb) | (uint64_t)k;
-        if (in_range(pos, len, st)) words[pos] = w;
+    constexpr int U = 4;   // index loads of U rounds go out before their atomics
+    const int64_t B = blockDim.x;
+    for (int64_t k0 = c0 + tid; k0 < c1; k0 += U * B) {
+        int32_t iv[U], jv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = k0 + u * B;
+            iv[u] = k < c1 ? ii[k] : 1;
+            jv[u] = k < c1 ? jj[k] : 1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t k = k0 + u * B;
+            if (k >= c1) break;
+            const uint32_t i0 = (uint32_t)(checked_index(iv[u], m, st) - 1);
+            const uint32_t j0 = (uint32_t)(checked_index(jv[u], n, st) - 1);
+            const uint32_t pos = atomicAdd(&s_cur[j0 >> cs], 1u);
+            const uint64_t w = ((uint64_t)(j0 & lowmask) << (rb + kb)) | ((uint64_t)i0 << kb) | (uint64_t)k;
+            if (in_range(pos, len, st)) words[pos] = w;
+        }
     }
 }
 
@@ -414,9 +428,15 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                 if (hi - lo > kRunSortMax) {
                     atomicOr(&a.st->overflow, 1u);   // redone by the onesweep path
                 } else {
+                    // Two words per 16-byte shared load (low words at 0 and 8).
                     const uint32_t kl = (uint32_t)v;
-                    int rank = 0;
-                    for (int q = lo; q < hi; ++q) rank += s_w32[2 * q] < kl;
+                    int rank = 0, q = lo;
+                    if (q & 1) rank += s_w32[2 * q++] < kl;
+                    for (; q + 1 < hi; q += 2) {
+                        const uint4 two = *reinterpret_cast<const uint4 *>(s_w32 + 2 * q);
+                        rank += (two.x < kl) + (two.z < kl);
+                    }
+                    if (q < hi) rank += s_w32[2 * q] < kl;
                     dest = lo + rank;
                 }
             }
