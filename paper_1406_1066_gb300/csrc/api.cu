@@ -527,7 +527,7 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
     bt->total_nnz = total_nnz;
     bt->h_len_off = new (std::nothrow) int64_t[count + 1];
     bt->h_nnz_off = new (std::nothrow) int64_t[count + 1];
-    bt->numeric_tile = 4096;
+    bt->numeric_tile = 1024;
     bt->nchunks = (total_len + kChunk - 1) / kChunk;
     auto fail = [&](fsparse_status st) {
         void *ptrs[2] = {bt->perm, bt->chunk_slot0};

@@ -44,7 +44,7 @@ struct Plan {
     int32_t *irS = nullptr;          // [max(len, nzmax, 1)]
     uint32_t *perm = nullptr;        // [len] sorted position -> k, kHeadBit on run heads
     uint32_t *chunk_slot0 = nullptr; // [nchunks+1] runs that start before each kChunk positions
-    int numeric_tile = 4096;         // positions per numeric block
+    int numeric_tile = 1024;         // positions per numeric block
     int64_t nchunks = 0;
     fsparse_config cfg{};            // configuration that built this plan
 };
@@ -57,7 +57,7 @@ struct Batch {
     int64_t *h_nnz_off = nullptr;    // host [count+1]
     uint32_t *perm = nullptr;        // [total_len], k offset into the concatenation
     uint32_t *chunk_slot0 = nullptr; // [nchunks+1]
-    int numeric_tile = 4096;
+    int numeric_tile = 1024;
     int64_t nchunks = 0;
 };
 
