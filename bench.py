@@ -43,10 +43,16 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 def workload_desc(t) -> str:
-    N = t.meta.get("N")
-    return (f"{t.name}: 3D P1 Kuhn-tetrahedral cube, {N}^3 vertices (m=n={t.m}), "
-            f"{(N - 1) ** 3 * 6} tets, L={t.L} int32 1-based triplets in element order, "
-            f"FP64 values U(-1,1); full assembly then {NUMERIC_STEPS} numeric re-assemblies")
+    N, dim = t.meta.get("N"), t.meta.get("dim")
+    tail = (f"L={t.L} int32 1-based triplets, FP64 values; full assembly then {NUMERIC_STEPS} "
+            f"numeric re-assemblies")
+    if dim == 3:
+        return (f"{t.name}: 3D P1 Kuhn-tetrahedral cube, {N}^3 vertices (m=n={t.m}), "
+                f"{(N - 1) ** 3 * 6} tets, element order, U(-1,1) values, {tail}")
+    if dim == 2:
+        return (f"{t.name}: 2D P1 triangulated square, {N}^2 vertices (m=n={t.m}), "
+                f"{(N - 1) ** 2 * 2} triangles, element order, U(-1,1) values, {tail}")
+    return f"{t.name}: m={t.m}, n={t.n}, {tail}"
 
 
 def hbm_peak():
