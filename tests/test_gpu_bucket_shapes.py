@@ -1,0 +1,53 @@
+"""Every shape of the column-bucket kernel, and bucket narrowing, against the
+oracle.  Inputs with exactly c triplets per column make the bucket sizes
+known: the width rule puts 2^cs columns in a bucket with c * 2^cs in
+(target / 2, target], so the largest bucket lands in a chosen capacity class
+(4096 -> 256 x 16, 6144 -> 512 x 12, 8192 -> 512 x 16)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_same, config, gpu_assemble
+
+pytestmark = pytest.mark.gpu
+
+
+def per_column(n_cols, c, m, seed, used_cols=None):
+    g = np.random.Generator(np.random.PCG64(seed))
+    cols = np.arange(1, (used_cols or n_cols) + 1, dtype=np.int32)
+    jj = np.repeat(cols, c)
+    g.shuffle(jj)
+    ii = g.integers(1, m + 1, jj.size, dtype=np.int32)
+    s = g.standard_normal(jj.size)
+    return ii, jj, s
+
+
+@pytest.mark.parametrize("c,target", [(32, 4096), (40, 8192), (100, 8192)],
+                         ids=["bucket_4096_256x16", "bucket_5120_512x12", "bucket_6400_512x16"])
+def test_bucket_shape(c, target):
+    n, m = 1 << 14, 5000
+    ii, jj, s = per_column(n, c, m, 61 + c)
+    with config(strategy=2, bucket_target=target):
+        g = gpu_assemble(ii, jj, s, m, n)
+    assert_same(g, oracle.assemble(ii, jj, s, m, n))
+
+
+def test_uneven_columns_narrow_the_buckets():
+    """Half the columns empty: the average suggests 6400 per bucket, the real
+    largest is 12800, so the buckets are halved before the scatter."""
+    n, m = 1 << 14, 5000
+    ii, jj, s = per_column(n, 100, m, 62, used_cols=n // 2)
+    with config(strategy=2, bucket_target=8192):
+        g = gpu_assemble(ii, jj, s, m, n)
+    assert_same(g, oracle.assemble(ii, jj, s, m, n))
+
+
+def test_three_pass_rows_without_stash_room():
+    """2^19 columns x 40, rows in [1, 60000]: 5120 per bucket, ~13 bits of row
+    ranks -> three sort passes, and k needs 25 bits, so the row offset does
+    not fit above the digits and rows are recovered from the rank bitmap."""
+    n, m = 1 << 19, 60000
+    ii, jj, s = per_column(n, 40, m, 63)
+    with config(strategy=2, bucket_target=8192):
+        g = gpu_assemble(ii, jj, s, m, n)
+    assert_same(g, oracle.assemble(ii, jj, s, m, n))
