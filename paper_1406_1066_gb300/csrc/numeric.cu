@@ -112,9 +112,15 @@ __global__ void __launch_bounds__(THREADS)
             double w[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) w[u] = u < c ? gather(sr, x[u], len) : 0.0;
+            // A warp-wide FP64 add costs the same issue time on GB300 however
+            // few lanes take part, so the adds stop at the largest count of
+            // the lanes still here (after the first batch usually one or two).
+            const int cmax = __reduce_max_sync(__activemask(), c);
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < 8; ++u) {
+                if (u >= cmax) break;
                 if (u < c) acc += w[u];
+            }
             if (c < 8) break;
             g += 8;
         }
