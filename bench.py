@@ -388,20 +388,50 @@ def gpu_arm(args):
         h_jc = torch.empty(t.n + 1, dtype=torch.int32).pin_memory()
         h_ir = torch.empty(L, dtype=torch.int32).pin_memory()
         d_s = torch.empty(L, dtype=torch.float64, device=dev)
+        # Host link: uploads of the next values overlap the current fold and
+        # the download of the previous result (one stream per direction).
+        vbuf = [torch.empty(L, dtype=torch.float64, device=dev) for _ in range(2)]
+        obuf = [torch.empty(L, dtype=torch.float64, device=dev) for _ in range(2)]
+        up_s, down_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
         def e2e_step():
+            cur = torch.cuda.current_stream()
+            up_done = [torch.cuda.Event() for _ in range(NUMERIC_STEPS)]
+            fold_done = [torch.cuda.Event() for _ in range(NUMERIC_STEPS)]
+            down_done = [torch.cuda.Event() for _ in range(NUMERIC_STEPS)]
+
+            def upload(r):
+                if r >= 2:
+                    up_s.wait_event(fold_done[r - 2])     # vbuf[r % 2] is free again
+                with torch.cuda.stream(up_s):
+                    vbuf[r % 2].copy_(h_vals[(r + 1) % 4], non_blocking=True)
+                up_done[r].record(up_s)
+
+            upload(0)                                     # overlaps the assembly below
             ii_d.copy_(h_ii, non_blocking=True)
             jj_d.copy_(h_jj, non_blocking=True)
             d_s.copy_(h_vals[0], non_blocking=True)
             jcS, irS, pr, plan = fsparse.assemble(ii_d, jj_d, d_s, t.m, t.n, prS=prS)
-            h_jc.copy_(jcS, non_blocking=True)
-            h_ir[: plan.nnz].copy_(irS[: plan.nnz], non_blocking=True)
-            h_out[: plan.nnz].copy_(pr[: plan.nnz], non_blocking=True)
-            for r in range(NUMERIC_STEPS):
-                d_s.copy_(h_vals[(r + 1) % 4], non_blocking=True)
-                fsparse.numeric(plan, d_s, out)
-                h_out[: plan.nnz].copy_(out[: plan.nnz], non_blocking=True)
             nz = plan.nnz
+            ev = torch.cuda.Event()
+            ev.record(cur)
+            down_s.wait_event(ev)
+            with torch.cuda.stream(down_s):
+                h_jc.copy_(jcS, non_blocking=True)
+                h_ir[:nz].copy_(irS[:nz], non_blocking=True)
+                h_out[:nz].copy_(pr[:nz], non_blocking=True)
+            for r in range(NUMERIC_STEPS):
+                if r + 1 < NUMERIC_STEPS:
+                    upload(r + 1)
+                cur.wait_event(up_done[r])
+                if r >= 2:
+                    cur.wait_event(down_done[r - 2])      # obuf[r % 2] has been read back
+                fsparse.numeric(plan, vbuf[r % 2], obuf[r % 2])
+                fold_done[r].record(cur)
+                down_s.wait_event(fold_done[r])
+                with torch.cuda.stream(down_s):
+                    h_out[:nz].copy_(obuf[r % 2][:nz], non_blocking=True)
+                down_done[r].record(down_s)
             torch.cuda.synchronize()
             plan.close()
             return nz
