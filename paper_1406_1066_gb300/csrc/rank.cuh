@@ -8,7 +8,8 @@
 // in shared memory.  A block-wide pass then turns the counts into exclusive
 // offsets ordered by (digit, warp), which makes the whole ranking stable.
 // (Finding peers with warp ballots takes one ballot per digit bit; a shared
-// atomicOr per item measured about four times faster on GB300.)
+// atomicOr per item measured about four times faster on GB300, and the full
+// bucket kernel ran 9% slower with __match_any_sync in its place.)
 #pragma once
 
 #include "common.cuh"
