@@ -242,11 +242,12 @@ fsparse_status fsparse_get_config(int64_t len, int32_t m, int32_t n, fsparse_con
    would otherwise apply.  Invalid values: FSPARSE_ERR_ARG.  Host only. */
 fsparse_status fsparse_set_config(const fsparse_config *cfg);
 
-/* Time every candidate configuration on the given device problem (the
-   inputs are only read) with CUDA events on `stream`, keep the fastest for
-   the problem's size class in the process-wide table, and report it in
-   *best (may be NULL).  `reps` timed runs per candidate (>= 1).  Allocates
-   and synchronises freely; not for use inside graph capture. */
+/* Tune on the given device problem (the inputs are only read), timing with
+   CUDA events on `stream`: first every sort configuration by the time of the
+   symbolic call (`reps` timed runs each, >= 1), then the numeric tile by
+   repeated folds on the winner's plan.  The result is kept for the problem's
+   size class in the process-wide table and reported in *best (may be NULL).
+   Allocates and synchronises freely; not for use inside graph capture. */
 fsparse_status fsparse_autotune(const int32_t *ii, const int32_t *jj, const double *sr,
                                 int64_t len, int32_t m, int32_t n, int32_t reps,
                                 void *stream, fsparse_config *best);

@@ -652,13 +652,14 @@ extern "C" fsparse_status fsparse_autotune(const int32_t *ii, const int32_t *jj,
     cudaEventCreate(&t1);
     float best_ms = 1e30f;
     fsparse_config best_cfg = resolve_config(len, key);
+    // 1. The sort configuration, by the time of the symbolic call alone.
     for (const fsparse_config &c : tune_candidates(len, key)) {
         std::vector<float> times;
         bool ok = true;
         for (int r = 0; r < reps + 1 && ok; ++r) {   // first run warms the pool and caches
             Plan *p = nullptr;
             cudaEventRecord(t0, s);
-            e = symbolic_impl(ii, jj, sr, prS, len, m, n, 0, s, &p, &c);
+            e = symbolic_impl(ii, jj, nullptr, nullptr, len, m, n, 0, s, &p, &c);
             cudaEventRecord(t1, s);
             cudaEventSynchronize(t1);
             if (e != FSPARSE_OK) {
@@ -681,6 +682,30 @@ extern "C" fsparse_status fsparse_autotune(const int32_t *ii, const int32_t *jj,
         if (med < best_ms) {
             best_ms = med;
             best_cfg = c;
+        }
+    }
+    // 2. The numeric tile, by repeated folds on the winner's plan (re-assembly
+    //    is where the fold's speed counts).
+    if (best_ms < 1e30f) {
+        Plan *p = nullptr;
+        if (symbolic_impl(ii, jj, nullptr, nullptr, len, m, n, 0, s, &p, &best_cfg) == FSPARSE_OK) {
+            float best_fold = 1e30f;
+            for (int tile : {1024, 2048, 4096}) {
+                const int folds = 4 * reps + 2;
+                bool ok = launch_numeric(p->perm, p->chunk_slot0, len, tile, sr, prS, p->nnz, p->cap, s) == FSPARSE_OK;
+                cudaEventRecord(t0, s);
+                for (int r = 0; r < folds && ok; ++r)
+                    ok = launch_numeric(p->perm, p->chunk_slot0, len, tile, sr, prS, p->nnz, p->cap, s) == FSPARSE_OK;
+                cudaEventRecord(t1, s);
+                cudaEventSynchronize(t1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (ok && ms < best_fold) {
+                    best_fold = ms;
+                    best_cfg.numeric_tile = tile;
+                }
+            }
+            fsparse_plan_destroy(reinterpret_cast<fsparse_plan>(p));
         }
     }
     cudaEventDestroy(t0);

@@ -73,17 +73,16 @@ void tune_store(int64_t len, const KeyLayout &key, const fsparse_config &cfg) {
 
 // Candidates: every onesweep shape, the bucket path at several bucket sizes,
 // each with the numeric tile sizes.
+// Sort candidates (the numeric tile is tuned separately, on the winner's plan).
 std::vector<fsparse_config> tune_candidates(int64_t len, const KeyLayout &key) {
     std::vector<fsparse_config> out;
-    const int tiles[3] = {1024, 2048, 4096};
-    for (int t : tiles) {
-        for (int r = 6; r <= 8; ++r)
-            for (int th : {256, 512})
-                for (int it : {8, 12, 16}) out.push_back(fsparse_config{FSPARSE_SORT_ONESWEEP, r, it, th, 8192, t});
-        for (int bt : {2048, 4096, 8192, 12288}) {
-            fsparse_config c{FSPARSE_SORT_BUCKET, 8, 16, 256, bt, t};
-            if (bucket_supported(len, 1 << key.cb, key, c)) out.push_back(c);
-        }
+    const int tile = default_config(len, key).numeric_tile;
+    for (int r = 6; r <= 8; ++r)
+        for (int th : {256, 512})
+            for (int it : {8, 12, 16}) out.push_back(fsparse_config{FSPARSE_SORT_ONESWEEP, r, it, th, 8192, tile});
+    for (int bt : {2048, 4096, 8192, 12288}) {
+        fsparse_config c{FSPARSE_SORT_BUCKET, 8, 16, 256, bt, tile};
+        if (bucket_supported(len, 1 << key.cb, key, c)) out.push_back(c);
     }
     return out;
 }
