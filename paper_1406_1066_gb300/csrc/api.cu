@@ -168,9 +168,12 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     if (!unfit) {
         e = FSPARSE_OK;
     } else {
-        if ((e = onesweep_sort(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan.perm, d_st, scratch, s)) != FSPARSE_OK)
+        const void *keys = nullptr;
+        int key_bytes = 0;
+        if ((e = onesweep_sort(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan.perm, &keys, &key_bytes, d_st,
+                               scratch, s)) != FSPARSE_OK)
             return e;
-        e = emit_from_perm(ii, jj, len, plan.m, plan.n, plan.key, plan, d_st, scratch, s);
+        e = emit_from_perm(keys, key_bytes, len, plan.n, plan.key, plan, d_st, scratch, s);
     }
     if (e != FSPARSE_OK) return e;
     if (sr) {

@@ -120,16 +120,19 @@ fsparse_status launch_minmax(const int32_t *ii, const int32_t *jj, int64_t len, 
                              int32_t n, DevStatus *st, cudaStream_t s);
 
 // Global stable LSD radix sort (one kernel per digit) producing perm[len]
-// (sorted position -> k).  Tile/radix from cfg.
+// (sorted position -> k) and the sorted (column, row) keys (*keys_out, in
+// scratch, *key_bytes = 4 or 8; NULL when every key is equal).  Tile/radix
+// from cfg.
 fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
                              int32_t n, const KeyLayout &key, const fsparse_config &cfg,
-                             uint32_t *perm_out, DevStatus *st, Scratch &scratch, cudaStream_t s);
+                             uint32_t *perm_out, const void **keys_out, int *key_bytes, DevStatus *st,
+                             Scratch &scratch, cudaStream_t s);
 
-// Run detection + slots + irank + irS + column counts + chunk slot bases
-// from a sorted perm (gathering the keys back from ii/jj).
-fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
-                              int32_t n, const KeyLayout &key, Plan &plan, DevStatus *st,
-                              Scratch &scratch, cudaStream_t s);
+// Run detection + slots + irS + column counts + chunk slot bases from a
+// sorted perm and its sorted keys.
+fsparse_status emit_from_perm(const void *keys, int key_bytes, int64_t len, int32_t n,
+                              const KeyLayout &key, Plan &plan, DevStatus *st, Scratch &scratch,
+                              cudaStream_t s);
 
 // Exclusive scan of counts[count] into out[count+1] (out[count] = total).
 fsparse_status exclusive_scan_u32(const uint32_t *counts, uint32_t *out, int64_t count,

@@ -87,9 +87,12 @@ extern "C" fsparse_status fsparse_assemble_noalloc(const int32_t *ii, const int3
     if (len == 0) {
         FSP_CUDA(cudaMemsetAsync(jcS, 0, ((size_t)n + 1) * 4, s));
     } else {
-        if ((e = onesweep_sort(ii, jj, len, m, n, plan.key, cfg, plan.perm, d_st, scratch, s)) != FSPARSE_OK)
+        const void *keys = nullptr;
+        int key_bytes = 0;
+        if ((e = onesweep_sort(ii, jj, len, m, n, plan.key, cfg, plan.perm, &keys, &key_bytes, d_st, scratch,
+                               s)) != FSPARSE_OK)
             return e;
-        if ((e = emit_from_perm(ii, jj, len, m, n, plan.key, plan, d_st, scratch, s)) != FSPARSE_OK)
+        if ((e = emit_from_perm(keys, key_bytes, len, n, plan.key, plan, d_st, scratch, s)) != FSPARSE_OK)
             return e;
         if ((e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s)) !=
             FSPARSE_OK)

@@ -115,6 +115,7 @@ struct PassArgs {
     void *kout;
     uint32_t *vout;
     int out_fmt;
+    int shift;                 // this pass's digit is (key >> shift) & (RADIX - 1)
     int64_t len;
     const uint32_t *bin_off;   // [RADIX] exclusive global offsets of this digit
     uint32_t *look;            // [ntiles][RADIX] look-back words
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         valid[i] = wbase + i * 32 < a.len;
-        dig[i] = (uint32_t)(key[i] & MASK);
+        dig[i] = (uint32_t)((key[i] >> a.shift) & MASK);
     }
     warp_rank<R, ITEMS>(dig, valid, s_wcnt + warp * RADIX, s_wm + warp * RADIX, rnk);
     __syncthreads();
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         if (wbase + i * 32 < a.len) {
-            const uint32_t d = (uint32_t)(key[i] & MASK);
+            const uint32_t d = dig[i];
             const uint32_t q = s_local[d] + s_wcnt[warp * RADIX + d] + rnk[i];
             if (in_range(q, count, a.st)) {
                 s_keys[q] = key[i];
@@ -234,13 +235,13 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
     __syncthreads();
     for (int j = tid; j < count; j += THREADS) {
         const uint64_t k = s_keys[j];
-        const uint32_t d = (uint32_t)(k & MASK);
+        const uint32_t d = (uint32_t)((k >> a.shift) & MASK);
         const int64_t g = (int64_t)s_global[d] + (j - (int64_t)s_local[d]);
         if (!in_range(g, a.len, a.st)) continue;
         if (a.out_fmt == FMT_U64)
-            static_cast<uint64_t *>(a.kout)[g] = k >> R;
+            static_cast<uint64_t *>(a.kout)[g] = k;
         else if (a.out_fmt == FMT_U32)
-            static_cast<uint32_t *>(a.kout)[g] = (uint32_t)(k >> R);
+            static_cast<uint32_t *>(a.kout)[g] = (uint32_t)k;
         a.vout[g] = s_vals[j];
     }
 }
@@ -288,7 +289,10 @@ static PassFn pick_pass(int R, int threads, int items) {
 
 fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
                              int32_t n, const KeyLayout &key, const fsparse_config &cfg,
-                             uint32_t *perm_out, DevStatus *st, Scratch &scratch, cudaStream_t s) {
+                             uint32_t *perm_out, const void **keys_out, int *key_bytes, DevStatus *st,
+                             Scratch &scratch, cudaStream_t s) {
+    *keys_out = nullptr;
+    *key_bytes = 0;
     const int KB = key.total();
     const int R = cfg.radix_bits;
     const int RADIX = 1 << R;
@@ -316,17 +320,19 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
     FSP_CUDA(cudaMemsetAsync(look, 0, (size_t)npass * ntiles * RADIX * 4, s));
     FSP_CUDA(cudaMemsetAsync(tickets, 0, (size_t)npass * 4, s));
 
-    // Remaining key after pass d holds KB - (d+1)R bits.
-    const bool wide = KB - R > 32;
+    // Every pass carries the whole key (digits are taken by shifting), so the
+    // sorted keys come out beside perm and the emit reads them in order
+    // instead of gathering ii/jj through perm.
+    const int kfmt = KB > 32 ? FMT_U64 : FMT_U32;
+    const size_t kbytes = KB > 32 ? 8 : 4;
     void *kbuf[2] = {nullptr, nullptr};
     uint32_t *vbuf[2] = {nullptr, nullptr};
-    const size_t kbytes = wide ? 8 : 4;
+    if ((e = scratch.alloc(&kbuf[0], (size_t)len * kbytes)) != FSPARSE_OK) return e;
     if (npass > 1) {
-        if ((e = scratch.alloc(&kbuf[0], (size_t)len * kbytes)) != FSPARSE_OK) return e;
+        if ((e = scratch.alloc(&kbuf[1], (size_t)len * kbytes)) != FSPARSE_OK) return e;
         if ((e = scratch.get(&vbuf[0], (size_t)len)) != FSPARSE_OK) return e;
     }
     if (npass > 2) {
-        if ((e = scratch.alloc(&kbuf[1], (size_t)len * kbytes)) != FSPARSE_OK) return e;
         if ((e = scratch.get(&vbuf[1], (size_t)len)) != FSPARSE_OK) return e;
     }
     for (int d = 0; d < npass; ++d) {
@@ -341,29 +347,25 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
         a.bin_off = offs + (size_t)d * RADIX;
         a.look = look + (size_t)d * ntiles * RADIX;
         a.ticket = tickets + d;
-        const int rem_in = KB - d * R, rem_out = KB - (d + 1) * R;
-        a.in_fmt = d == 0 ? FMT_IJ : (rem_in > 32 ? FMT_U64 : FMT_U32);
+        a.shift = d * R;
+        a.in_fmt = d == 0 ? FMT_IJ : kfmt;
         a.kin = d == 0 ? nullptr : kbuf[(d - 1) & 1];
         a.vin = d == 0 ? nullptr : vbuf[(d - 1) & 1];
-        if (d == npass - 1) {
-            a.out_fmt = FMT_NONE;
-            a.kout = nullptr;
-            a.vout = perm_out;
-        } else {
-            a.out_fmt = rem_out > 32 ? FMT_U64 : FMT_U32;
-            a.kout = kbuf[d & 1];
-            a.vout = vbuf[d & 1];
-        }
+        a.out_fmt = kfmt;
+        a.kout = kbuf[d & 1];
+        a.vout = d == npass - 1 ? perm_out : vbuf[d & 1];
         if ((e = pass(a, ntiles, s)) != FSPARSE_OK) return e;
     }
+    *keys_out = kbuf[(npass - 1) & 1];
+    *key_bytes = (int)kbytes;
     return FSPARSE_OK;
 }
 
 // ----------------------------------------------------------------------------
 // Emit: runs, slots, irS, column counts and numeric chunk slot bases.
 struct EmitArgs {
-    const int32_t *ii, *jj;
-    int32_t m, n;
+    const void *keys;        // sorted (column, row) keys, key_bytes wide; NULL: all equal
+    int key_bytes;
     int rb;
     uint32_t *perm;          // in: sorted k, out: k | kHeadBit on run heads
     int32_t *irS;
@@ -375,6 +377,12 @@ struct EmitArgs {
     uint32_t *ticket;
     DevStatus *st;
 };
+
+__device__ __forceinline__ uint64_t sorted_key(const EmitArgs &a, int64_t p) {
+    if (!a.keys) return 0;
+    return a.key_bytes == 8 ? static_cast<const uint64_t *>(a.keys)[p]
+                            : static_cast<const uint32_t *>(a.keys)[p];
+}
 
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
@@ -403,21 +411,10 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
         for (int i = 0; i < ITEMS; ++i) k[i] = p0 + i < a.len ? a.perm[p0 + i] : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        key[i] = 0;
-        if (p0 + i < a.len) {
-            uint32_t kk = k[i] & kIndexMask;
-            if (!in_range(kk, a.len, a.st)) kk = 0;
-            key[i] = make_key(checked_index(a.ii[kk], a.m, a.st), checked_index(a.jj[kk], a.n, a.st), a.rb);
-        }
-    }
+    for (int i = 0; i < ITEMS; ++i) key[i] = p0 + i < a.len ? sorted_key(a, p0 + i) : 0;
     // Key of the position just before this thread's first one.
     uint64_t prev = __shfl_up_sync(0xffffffffu, key[ITEMS - 1], 1);
-    if (lane == 0 && p0 > 0 && p0 <= a.len) {
-        uint32_t kk = a.perm[p0 - 1] & kIndexMask;
-        if (!in_range(kk, a.len, a.st)) kk = 0;
-        prev = make_key(checked_index(a.ii[kk], a.m, a.st), checked_index(a.jj[kk], a.n, a.st), a.rb);
-    }
+    if (lane == 0 && p0 > 0 && p0 <= a.len) prev = sorted_key(a, p0 - 1);
     uint32_t heads = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -483,9 +480,9 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
     }
 }
 
-fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
-                              int32_t n, const KeyLayout &key, Plan &plan, DevStatus *st,
-                              Scratch &scratch, cudaStream_t s) {
+fsparse_status emit_from_perm(const void *keys, int key_bytes, int64_t len, int32_t n,
+                              const KeyLayout &key, Plan &plan, DevStatus *st, Scratch &scratch,
+                              cudaStream_t s) {
     constexpr int THREADS = 256, ITEMS = 8, TILE = THREADS * ITEMS;
     const int64_t ntiles = (len + TILE - 1) / TILE;
     uint32_t *colcnt, *look, *ticket;
@@ -498,10 +495,8 @@ fsparse_status emit_from_perm(const int32_t *ii, const int32_t *jj, int64_t len,
     FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
     if (len > 0) {
         EmitArgs a{};
-        a.ii = ii;
-        a.jj = jj;
-        a.m = m;
-        a.n = n;
+        a.keys = keys;
+        a.key_bytes = key_bytes;
         a.rb = key.rb;
         a.perm = plan.perm;
         a.irS = plan.irS;

@@ -58,6 +58,7 @@ def same(a, b):
 def test_noalloc_matches_assemble_on_consecutive_calls():
     problems = [inputs.mesh3d(12, 5),                                     # 116,160 triplets
                 inputs.random_small(MAX_LEN, 3000, 4000, 9, dup=0.4),    # the size limit
+                inputs.random_small(MAX_LEN, MAX_LEN, MAX_LEN, 12, dup=0.4),  # widest keys (64-bit)
                 inputs.random_small(333, 7, 5, 10, dup=0.6)]             # small after large
     for t in problems:
         ref = reference(t)
