@@ -70,25 +70,48 @@ __device__ __forceinline__ uint64_t make_key(int32_t i, int32_t j, int rb) {
 }
 
 // ----------------------------------------------------------------------------
-// All digit histograms in one read of ii/jj (validation fused).
+// All digit histograms in one read of ii/jj (validation fused).  Every warp
+// counts into its own copy of the tables (fewer colliding shared atomics),
+// and each thread takes four triplets per step (16-byte loads when aligned).
+template <int R>
+__device__ __forceinline__ void hist_add(uint32_t *my, uint64_t key, int npass) {
+    constexpr int RADIX = 1 << R;
+    for (int d = 0; d < npass; ++d) atomicAdd(&my[d * RADIX + (int)((key >> (d * R)) & (RADIX - 1))], 1u);
+}
+
 template <int R>
 __global__ void digit_hist_kernel(const int32_t *__restrict__ ii, const int32_t *__restrict__ jj,
                                   int64_t len, int32_t m, int32_t n, int rb, int npass,
                                   uint32_t *hist, DevStatus *st) {
     constexpr int RADIX = 1 << R;
-    extern __shared__ uint32_t s_hist[];
-    const int nb = npass * RADIX;
-    for (int t = threadIdx.x; t < nb; t += blockDim.x) s_hist[t] = 0;
+    extern __shared__ uint32_t s_hist[];   // [warps][npass * RADIX]
+    const int nb = npass * RADIX, warps = blockDim.x >> 5;
+    uint32_t *my = s_hist + (threadIdx.x >> 5) * nb;
+    for (int t = threadIdx.x; t < warps * nb; t += blockDim.x) s_hist[t] = 0;
     __syncthreads();
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < len;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t key = make_key(checked_index(ii[k], m, st), checked_index(jj[k], n, st), rb);
-        for (int d = 0; d < npass; ++d)
-            atomicAdd(&s_hist[d * RADIX + (int)((key >> (d * R)) & (RADIX - 1))], 1u);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(ii) | reinterpret_cast<uintptr_t>(jj)) & 15) == 0) {
+        const int64_t n4 = len / 4;
+        for (int64_t q = t0; q < n4; q += stride) {
+            const int4 a = reinterpret_cast<const int4 *>(ii)[q];
+            const int4 b = reinterpret_cast<const int4 *>(jj)[q];
+            hist_add<R>(my, make_key(checked_index(a.x, m, st), checked_index(b.x, n, st), rb), npass);
+            hist_add<R>(my, make_key(checked_index(a.y, m, st), checked_index(b.y, n, st), rb), npass);
+            hist_add<R>(my, make_key(checked_index(a.z, m, st), checked_index(b.z, n, st), rb), npass);
+            hist_add<R>(my, make_key(checked_index(a.w, m, st), checked_index(b.w, n, st), rb), npass);
+        }
+        done = n4 * 4;
     }
+    for (int64_t k = done + t0; k < len; k += stride)
+        hist_add<R>(my, make_key(checked_index(ii[k], m, st), checked_index(jj[k], n, st), rb), npass);
     __syncthreads();
-    for (int t = threadIdx.x; t < nb; t += blockDim.x)
-        if (s_hist[t]) atomicAdd(&hist[t], s_hist[t]);
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        uint32_t c = 0;
+        for (int w = 0; w < warps; ++w) c += s_hist[w * nb + t];
+        if (c) atomicAdd(&hist[t], c);
+    }
 }
 
 template <int R>
@@ -264,7 +287,9 @@ static fsparse_status run_hist(const int32_t *ii, const int32_t *jj, int64_t len
     constexpr int RADIX = 1 << R;
     int grid = (int)std::min<int64_t>((len + 4095) / 4096, (int64_t)sm_count(0) * 4);
     grid = std::max(grid, 1);
-    digit_hist_kernel<R><<<grid, 256, npass * RADIX * 4, s>>>(ii, jj, len, m, n, rb, npass, hist, st);
+    const size_t smem = (size_t)(256 / 32) * npass * RADIX * 4;
+    FSP_CUDA(cudaFuncSetAttribute(digit_hist_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    digit_hist_kernel<R><<<grid, 256, smem, s>>>(ii, jj, len, m, n, rb, npass, hist, st);
     FSP_LAUNCHED();
     digit_offsets_kernel<R><<<npass, RADIX, 0, s>>>(hist, offs);
     FSP_LAUNCHED();
