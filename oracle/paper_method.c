@@ -149,20 +149,29 @@ int64_t paper_sparse_omp(const int32_t *ii, const int32_t *jj, const double *sr,
         /* Part 1: private row counts over this thread's input slice. */
         for (int64_t k = k0; k < k1; k++) mycur[ii[k]]++;
 #pragma omp barrier
-        /* Per row: start of the row, then each thread's cursor after the
-           threads before it (thread order = input order: stable). */
+        /* Per row, in parallel: each thread's offset inside the row (the
+           threads before it come first: input order, so rank stays stable)
+           and the row's total; then the serial prefix over rows only (the
+           one strictly serial step, length M); then the row starts added. */
+#pragma omp for schedule(static)
+        for (int32_t r = 1; r <= M; r++) {
+            int64_t run = 0;
+            for (int u = 0; u < T; u++) {
+                int64_t *c = rowcur + (size_t)u * ((size_t)M + 1) + r;
+                const int64_t cnt = *c;
+                *c = run;
+                run += cnt;
+            }
+            rowend[r] = run;
+        }
 #pragma omp single
         {
-            int64_t run = 0;
-            for (int32_t r = 1; r <= M; r++) {
-                for (int u = 0; u < T; u++) {
-                    int64_t *c = rowcur + (size_t)u * ((size_t)M + 1) + r;
-                    const int64_t cnt = *c;
-                    *c = run;
-                    run += cnt;
-                }
-                rowend[r] = run;
-            }
+            for (int32_t r = 1; r <= M; r++) rowend[r] += rowend[r - 1];
+        }
+#pragma omp for schedule(static)
+        for (int32_t r = 1; r <= M; r++) {
+            const int64_t start = rowend[r - 1];
+            for (int u = 0; u < T; u++) rowcur[(size_t)u * ((size_t)M + 1) + r] += start;
         }
         /* Part 2: place this slice's triplets. */
         for (int64_t k = k0; k < k1; k++) rank[mycur[ii[k]]++] = k;
@@ -188,21 +197,28 @@ int64_t paper_sparse_omp(const int32_t *ii, const int32_t *jj, const double *sr,
         }
 #pragma omp barrier
         /* Part 4: per column, thread u's slots follow those of threads < u
-           (their rows are smaller); jcS from the totals. */
+           (their rows are smaller); the same three steps as for the rows. */
+#pragma omp for schedule(static)
+        for (int32_t c = 1; c <= N; c++) {
+            int64_t run = 0;
+            for (int u = 0; u < T; u++) {
+                int64_t *p = colcnt + (size_t)u * ((size_t)N + 1) + c;
+                const int64_t cnt = *p;
+                *p = run;
+                run += cnt;
+            }
+            jcS[c] = (int32_t)run;
+        }
 #pragma omp single
         {
-            int64_t run = 0;
             jcS[0] = 0;
-            for (int32_t c = 1; c <= N; c++) {
-                for (int u = 0; u < T; u++) {
-                    int64_t *p = colcnt + (size_t)u * ((size_t)N + 1) + c;
-                    const int64_t cnt = *p;
-                    *p = run;
-                    run += cnt;
-                }
-                jcS[c] = (int32_t)run;
-            }
-            nnz = run;
+            for (int32_t c = 1; c <= N; c++) jcS[c] += jcS[c - 1];
+            nnz = jcS[N];
+        }
+#pragma omp for schedule(static)
+        for (int32_t c = 1; c <= N; c++) {
+            const int64_t start = jcS[c - 1];
+            for (int u = 0; u < T; u++) colcnt[(size_t)u * ((size_t)N + 1) + c] += start;
         }
         for (int64_t i = i0; i < i1; i++) irankP[i] += (int32_t)mycol[jj[rank[i]]];
         /* Post-processing over the same rows: each slot's triplets are in
