@@ -6,6 +6,7 @@
 // bucket.cu, scan.cu and numeric.cu.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -68,8 +69,17 @@ static fsparse_status ensure_pool(int dev) {
     return FSPARSE_OK;
 }
 
+int injected_fault() {
+    const char *f = std::getenv("FSPARSE_FAULT");
+    if (!f || !*f) return FAULT_NONE;
+    if (std::strcmp(f, "alloc") == 0) return FAULT_ALLOC;
+    if (std::strcmp(f, "timeout") == 0) return FAULT_TIMEOUT;
+    return FAULT_NONE;
+}
+
 fsparse_status device_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
+    if (injected_fault() == FAULT_ALLOC) return set_error(FSPARSE_ERR_NOMEM, "injected allocation failure (FSPARSE_FAULT=alloc)");
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {

@@ -64,6 +64,15 @@ struct Batch {
 // ---- errors ---------------------------------------------------------------
 fsparse_status set_error(fsparse_status st, const std::string &msg);
 fsparse_status cuda_error(cudaError_t e, const char *what);
+
+// Host-side fault injection for the failure paths, read from the environment
+// at each call: FSPARSE_FAULT=alloc makes every device allocation report
+// out-of-memory; FSPARSE_FAULT=timeout makes the first tile of each
+// look-back scan withhold its prefix, so the following tiles' bounded waits
+// run out and the call returns FSPARSE_ERR_TIMEOUT.  Nothing faults, traps or
+// hangs the GPU; unset, it costs one getenv per call.
+enum InjectedFault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2 };
+int injected_fault();
 #define FSP_CUDA(call)                                                        \
     do {                                                                      \
         cudaError_t e_ = (call);                                              \

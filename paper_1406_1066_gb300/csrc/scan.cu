@@ -15,7 +15,7 @@ namespace fsp {
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS)
     scan_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t count,
-                uint32_t *look, uint32_t *ticket, DevStatus *st) {
+                uint32_t *look, uint32_t *ticket, DevStatus *st, int withhold_first) {
     constexpr int TILE = THREADS * ITEMS;
     __shared__ uint32_t s_scan[THREADS / 32 + 1];
     __shared__ uint32_t s_tile, s_excl;
@@ -36,7 +36,9 @@ __global__ void __launch_bounds__(THREADS)
     if (tid < 32) {
         uint32_t *word = look + tile;
         uint32_t excl = 0;
-        if (tid == 0) st_release(word, (tile == 0 ? kFlagInc : kFlagAgg) | tile_sum);
+        // (withhold_first: injected failure -- tile 0 never publishes, so the
+        // bounded waits of the following tiles run out)
+        if (tid == 0 && !(withhold_first && tile == 0)) st_release(word, (tile == 0 ? kFlagInc : kFlagAgg) | tile_sum);
         if (tile > 0) {
             excl = warp_lookback_exclusive(look, 1, tile, st);
             if (tid == 0) st_release(word, kFlagInc | (excl + tile_sum));
@@ -70,7 +72,8 @@ fsparse_status exclusive_scan_u32(const uint32_t *counts, uint32_t *out, int64_t
     if ((e = scratch.get(&ticket, 1)) != FSPARSE_OK) return e;
     FSP_CUDA(cudaMemsetAsync(look, 0, (size_t)ntiles * 4, s));
     FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
-    scan_kernel<THREADS, ITEMS><<<(unsigned)ntiles, THREADS, 0, s>>>(counts, out, count, look, ticket, st);
+    const int withhold = injected_fault() == FAULT_TIMEOUT ? 1 : 0;
+    scan_kernel<THREADS, ITEMS><<<(unsigned)ntiles, THREADS, 0, s>>>(counts, out, count, look, ticket, st, withhold);
     FSP_LAUNCHED();
     return FSPARSE_OK;
 }

@@ -1,0 +1,41 @@
+"""Failure paths, injected on the host (FSPARSE_FAULT): an allocation that
+fails, and a look-back wait that runs out because a predecessor tile never
+publishes.  Nothing faults, traps or hangs the GPU: the bounded wait gives up,
+the call returns its status, and the next call on the same context is exact."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_same, config, gpu_assemble, to_dev
+from paper_1406_1066_gb300 import fsparse, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_injected_allocation_failure(monkeypatch):
+    t = inputs.random_small(5000, 60, 50, 71, dup=0.3)
+    monkeypatch.setenv("FSPARSE_FAULT", "alloc")
+    with pytest.raises(fsparse.FsparseError) as e:
+        fsparse.assemble(to_dev(t.ii), to_dev(t.jj), to_dev(t.s), t.m, t.n)
+    assert e.value.status == fsparse.ERR_NOMEM
+    monkeypatch.delenv("FSPARSE_FAULT")
+    assert_same(gpu_assemble(t.ii, t.jj, t.s, t.m, t.n), oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
+
+
+def test_injected_lookback_timeout(monkeypatch):
+    """The column-pointer scan of the onesweep path spans several tiles
+    (8000 columns); with tile 0 withheld the others wait out their bound."""
+    t = inputs.mesh3d(20, 72)
+    with config(strategy=1):
+        monkeypatch.setenv("FSPARSE_FAULT", "timeout")
+        t0 = time.perf_counter()
+        with pytest.raises(fsparse.FsparseError) as e:
+            fsparse.symbolic(to_dev(t.ii), to_dev(t.jj), t.m, t.n)
+        waited = time.perf_counter() - t0
+        assert e.value.status == fsparse.ERR_TIMEOUT
+        assert waited < 60.0
+        monkeypatch.delenv("FSPARSE_FAULT")
+        g = gpu_assemble(t.ii, t.jj, t.s, t.m, t.n)
+    assert_same(g, oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
