@@ -69,6 +69,66 @@ static fsparse_status ensure_pool(int dev) {
     return FSPARSE_OK;
 }
 
+// ---- phase timing ----------------------------------------------------------------
+namespace {
+struct PhaseTimer {
+    static constexpr int kMax = 24;
+    cudaStream_t s = nullptr;
+    int n = 0;
+    cudaEvent_t ev[kMax];
+    const char *name[kMax];
+};
+thread_local PhaseTimer *t_timer = nullptr;
+thread_local std::vector<std::pair<const char *, double>> t_last;
+
+bool timing_requested() {
+    const char *t = std::getenv("FSPARSE_TIMING");
+    return t && t[0] == '1';
+}
+
+// Starts a timer for the calling thread when FSPARSE_TIMING=1 (RAII: the
+// durations are stored on finish(), the events always destroyed).
+struct TimerScope {
+    PhaseTimer timer;
+    bool on = false;
+    explicit TimerScope(cudaStream_t s) {
+        if (t_timer) return;   // nested call: the outer call's timer keeps running
+        t_last.clear();
+        if (!timing_requested()) return;
+        timer.s = s;
+        if (cudaEventCreate(&timer.ev[0]) != cudaSuccess) return;
+        cudaEventRecord(timer.ev[0], s);
+        timer.name[0] = "start";
+        timer.n = 1;
+        t_timer = &timer;
+        on = true;
+    }
+    void finish() {
+        if (!on || timer.n < 2) return;
+        cudaEventSynchronize(timer.ev[timer.n - 1]);
+        t_last.clear();
+        for (int i = 1; i < timer.n; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, timer.ev[i - 1], timer.ev[i]);
+            t_last.emplace_back(timer.name[i], (double)ms);
+        }
+    }
+    ~TimerScope() {
+        if (!on) return;
+        for (int i = 0; i < timer.n; ++i) cudaEventDestroy(timer.ev[i]);
+        t_timer = nullptr;
+    }
+};
+}  // namespace
+
+void phase_mark(const char *name) {
+    PhaseTimer *t = t_timer;
+    if (!t || t->n >= PhaseTimer::kMax) return;
+    if (cudaEventCreate(&t->ev[t->n]) != cudaSuccess) return;
+    cudaEventRecord(t->ev[t->n], t->s);
+    t->name[t->n++] = name;
+}
+
 int injected_fault() {
     const char *f = std::getenv("FSPARSE_FAULT");
     if (!f || !*f) return FAULT_NONE;
@@ -189,6 +249,7 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     if (sr) {
         e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s);
         if (e == FSPARSE_OK) *folded = true;
+        phase_mark("numeric_fold");
     }
     return e;
 }
@@ -204,6 +265,7 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     FSP_CUDA(cudaGetDevice(&dev));
     if ((e = ensure_pool(dev)) != FSPARSE_OK) return e;
 
+    TimerScope timing(s);
     Scratch scratch(s);
     DevStatus *d_st = nullptr;
     DevStatus h_st{};
@@ -212,6 +274,7 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
 
     if (m == 0 || n == 0) {   // implicit dimensions (§2.2): one extra synchronisation
         if ((e = launch_minmax(ii, jj, len, m, n, d_st, s)) != FSPARSE_OK) return e;
+        phase_mark("dims");
         if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return e;
         if (h_st.bad_index) return set_error(FSPARSE_ERR_INDEX, "index below 1 or above its dimension");
         if (m == 0) m = h_st.max_i;
@@ -275,7 +338,9 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     plan->cap = std::max(nnz, nzmax);
     if (plan->cap > nnz) {
         if ((e = launch_fill(plan->irS, folded ? prS : nullptr, nnz, plan->cap, s)) != FSPARSE_OK) return fail(e);
+        phase_mark("nzmax_tail");
     }
+    timing.finish();
     *out = plan;
     return FSPARSE_OK;
 }
@@ -444,6 +509,16 @@ fsparse_status fsparse_assemble_f64(const double *ii, const double *jj, const do
     int32_t *i32 = nullptr, *j32 = nullptr;
     if ((e = getix_pair(ii, jj, len, scratch, &i32, &j32, s)) != FSPARSE_OK) return e;
     return fsparse_assemble(i32, j32, sr, len, m, n, nzmax, prS, prS_capacity, stream, plan_out);
+}
+
+// ---- phase timing ------------------------------------------------------------
+int32_t fsparse_last_timings(const char **names, double *ms, int32_t max) {
+    const int32_t n = (int32_t)t_last.size();
+    for (int32_t i = 0; i < n && i < max; ++i) {
+        if (names) names[i] = t_last[i].first;
+        if (ms) ms[i] = t_last[i].second;
+    }
+    return n;
 }
 
 // ---- delayed assembly ---------------------------------------------------------

@@ -560,6 +560,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         }
     }
     sh.grid = G;
+    phase_mark("bucket_count");
     FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)nb + 1) * 4, s));
     FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
     if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
@@ -568,6 +569,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
                                                  words, st);
     FSP_LAUNCHED();
+    phase_mark("bucket_scatter");
 
     BucketEmitArgs a{};
     a.words = words;
@@ -586,9 +588,11 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     a.look = look;
     a.ticket = ticket;
     a.st = st;
-    if (largest <= (uint32_t)kEmitCap[0]) return run_emit<256, 16>(a, nb, s);
-    if (largest <= (uint32_t)kEmitCap[1]) return run_emit<512, 12>(a, nb, s);
-    return run_emit<512, 16>(a, nb, s);
+    if (largest <= (uint32_t)kEmitCap[0]) e = run_emit<256, 16>(a, nb, s);
+    else if (largest <= (uint32_t)kEmitCap[1]) e = run_emit<512, 12>(a, nb, s);
+    else e = run_emit<512, 16>(a, nb, s);
+    phase_mark("bucket_emit");
+    return e;
 }
 
 }  // namespace fsp

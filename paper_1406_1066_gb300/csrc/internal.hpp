@@ -73,6 +73,13 @@ fsparse_status cuda_error(cudaError_t e, const char *what);
 // hangs the GPU; unset, it costs one getenv per call.
 enum InjectedFault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2 };
 int injected_fault();
+
+// Per-phase timing of one symbolic call with CUDA events on its stream, on
+// when FSPARSE_TIMING=1.  symbolic_impl owns the timer of the calling thread;
+// the host launchers mark the end of each phase with phase_mark(name), which
+// does nothing when timing is off.  The durations of the thread's last timed
+// call are read with fsparse_last_timings.
+void phase_mark(const char *name);
 #define FSP_CUDA(call)                                                        \
     do {                                                                      \
         cudaError_t e_ = (call);                                              \

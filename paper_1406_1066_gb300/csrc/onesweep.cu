@@ -336,6 +336,7 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
     else if (R == 7) e = run_hist<7>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
     else e = run_hist<8>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
     if (e != FSPARSE_OK) return e;
+    phase_mark("digit_hist");
 
     const int64_t tile = (int64_t)cfg.sweep_threads * cfg.sweep_items;
     const int64_t ntiles = (len + tile - 1) / tile;
@@ -383,6 +384,7 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
     }
     *keys_out = kbuf[(npass - 1) & 1];
     *key_bytes = (int)kbytes;
+    phase_mark("digit_passes");
     return FSPARSE_OK;
 }
 
@@ -534,8 +536,11 @@ fsparse_status emit_from_perm(const void *keys, int key_bytes, int64_t len, int3
         a.st = st;
         emit_kernel<THREADS, ITEMS><<<(unsigned)ntiles, THREADS, 0, s>>>(a);
         FSP_LAUNCHED();
+        phase_mark("emit");
     }
-    return exclusive_scan_u32(colcnt, reinterpret_cast<uint32_t *>(plan.jcS), n, st, scratch, s);
+    e = exclusive_scan_u32(colcnt, reinterpret_cast<uint32_t *>(plan.jcS), n, st, scratch, s);
+    phase_mark("jcS_scan");
+    return e;
 }
 
 }  // namespace fsp

@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
     L.fsparse_last_error_string.restype = ctypes.c_char_p
     L.fsparse_status_string.argtypes = [ctypes.c_int]
     L.fsparse_status_string.restype = ctypes.c_char_p
+    L.fsparse_last_timings.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double), _I32]
+    L.fsparse_last_timings.restype = _I32
     L.fsparse_kernel_launches.argtypes = []
     L.fsparse_kernel_launches.restype = _I64
     _lib = L
@@ -237,6 +239,14 @@ def fsparse_tune_load(path: str) -> None:
 
 def fsparse_tune_clear() -> None:
     _check(lib().fsparse_tune_clear(), "fsparse_tune_clear")
+
+
+def fsparse_last_timings() -> List[Tuple[str, float]]:
+    """(phase, ms) of this thread's last symbolic/assemble call run with FSPARSE_TIMING=1."""
+    names = (ctypes.c_char_p * 32)()
+    ms = (ctypes.c_double * 32)()
+    n = lib().fsparse_last_timings(names, ms, 32)
+    return [(names[i].decode(), ms[i]) for i in range(min(n, 32))]
 
 
 def fsparse_kernel_launches() -> int:

@@ -39,3 +39,20 @@ def test_injected_lookback_timeout(monkeypatch):
         monkeypatch.delenv("FSPARSE_FAULT")
         g = gpu_assemble(t.ii, t.jj, t.s, t.m, t.n)
     assert_same(g, oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
+
+
+@pytest.mark.parametrize("strategy,phases", [
+    (2, ["bucket_count", "bucket_scatter", "bucket_emit", "numeric_fold"]),
+    (1, ["digit_hist", "digit_passes", "emit", "jcS_scan", "numeric_fold"])], ids=["bucket", "onesweep"])
+def test_phase_timing(monkeypatch, strategy, phases):
+    """FSPARSE_TIMING=1 records the device time of every phase of the call."""
+    t = inputs.mesh3d(16, 73)
+    with config(strategy=strategy):
+        monkeypatch.setenv("FSPARSE_TIMING", "1")
+        gpu_assemble(t.ii, t.jj, t.s, t.m, t.n)
+        got = fsparse.fsparse_last_timings()
+        monkeypatch.delenv("FSPARSE_TIMING")
+        assert [n for n, _ in got] == phases
+        assert all(ms >= 0.0 for _, ms in got) and sum(ms for _, ms in got) > 0.0
+        gpu_assemble(t.ii, t.jj, t.s, t.m, t.n)
+        assert fsparse.fsparse_last_timings() == []          # a call without it records nothing
