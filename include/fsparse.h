@@ -106,6 +106,22 @@ fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank,
 
 /* Release a plan (NULL is a no-op).  Waits for outstanding device work that
    may still read the plan's arrays. */
+/* Checkpoint and resume of the reusable symbolic state (re-assembly with the
+   same pattern after a restart).  fsparse_plan_export copies the plan into a
+   host buffer: a header (sizes, configuration) followed by perm, the numeric
+   chunk slot bases, jcS and irS; irank is not stored (it is derived again on
+   first request).  With host_buf == NULL it only reports the size in
+   *bytes_out.  Synchronous (blocking copies).  fsparse_plan_import checks
+   the header and every size against `bytes` before touching the device
+   (FSPARSE_ERR_ARG on any mismatch), then builds a new plan on the current
+   device, copying on `stream` and synchronising it before returning.  An
+   imported plan behaves exactly like the exported one.  The paper has no
+   counterpart (it keeps its state in memory between calls, §2). */
+fsparse_status fsparse_plan_export(fsparse_plan plan, void *host_buf, int64_t capacity,
+                                   int64_t *bytes_out);
+fsparse_status fsparse_plan_import(const void *host_buf, int64_t bytes, void *stream,
+                                   fsparse_plan *plan_out);
+
 /* Delayed assembly (§2 names input that is not all available at the first
    call as an extension of the method): a NEW plan for the concatenation of
    the plan's triplets and (ii, jj), device int32[len] unit-offset, whose

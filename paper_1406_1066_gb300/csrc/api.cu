@@ -6,6 +6,7 @@
 // bucket.cu, scan.cu and numeric.cu.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -509,6 +510,111 @@ fsparse_status fsparse_assemble_f64(const double *ii, const double *jj, const do
     int32_t *i32 = nullptr, *j32 = nullptr;
     if ((e = getix_pair(ii, jj, len, scratch, &i32, &j32, s)) != FSPARSE_OK) return e;
     return fsparse_assemble(i32, j32, sr, len, m, n, nzmax, prS, prS_capacity, stream, plan_out);
+}
+
+// ---- checkpoint: plan export / import -------------------------------------------
+// Layout: PlanImage header, then perm[len] u32, chunk_slot0[nchunks + 1] u32,
+// jcS[n + 1] i32, irS[cap] i32 (little-endian, as in device memory).  irank is
+// not stored: it is derived again on first request.
+struct PlanImage {
+    char magic[8];          // "FSPPLAN1"
+    int64_t m, n, len, nnz, cap, nchunks;
+    int32_t strategy, radix_bits, sweep_items, sweep_threads, bucket_target, numeric_tile;
+};
+
+static int64_t image_bytes(const PlanImage &h) {
+    return (int64_t)sizeof(PlanImage) + 4 * (h.len + (h.nchunks + 1) + (h.n + 1) + h.cap);
+}
+
+fsparse_status fsparse_plan_export(fsparse_plan plan, void *host_buf, int64_t capacity, int64_t *bytes_out) {
+    if (!plan || !bytes_out) return set_error(FSPARSE_ERR_ARG, "plan or bytes_out is NULL");
+    const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
+    PlanImage h{};
+    std::memcpy(h.magic, "FSPPLAN1", 8);
+    h.m = p.m; h.n = p.n; h.len = p.len; h.nnz = p.nnz; h.cap = p.cap; h.nchunks = p.nchunks;
+    h.strategy = p.cfg.strategy; h.radix_bits = p.cfg.radix_bits; h.sweep_items = p.cfg.sweep_items;
+    h.sweep_threads = p.cfg.sweep_threads; h.bucket_target = p.cfg.bucket_target; h.numeric_tile = p.numeric_tile;
+    *bytes_out = image_bytes(h);
+    if (!host_buf) return FSPARSE_OK;   // size query
+    if (capacity < *bytes_out) return set_error(FSPARSE_ERR_ARG, "host buffer smaller than the plan image");
+    char *out = static_cast<char *>(host_buf);
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p.device) cudaSetDevice(p.device);
+    auto get = [&](const void *src, int64_t count) {
+        const cudaError_t e = count > 0 ? cudaMemcpy(out + off, src, (size_t)count * 4, cudaMemcpyDeviceToHost)
+                                        : cudaSuccess;
+        off += (size_t)count * 4;
+        return e;
+    };
+    cudaError_t e = get(p.perm, p.len);
+    if (e == cudaSuccess) e = get(p.chunk_slot0, p.nchunks + 1);
+    if (e == cudaSuccess) e = get(p.jcS, (int64_t)p.n + 1);
+    if (e == cudaSuccess) e = get(p.irS, p.cap);
+    if (cur != p.device) cudaSetDevice(cur);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy (plan export)");
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_plan_import(const void *host_buf, int64_t bytes, void *stream, fsparse_plan *plan_out) {
+    if (!plan_out) return set_error(FSPARSE_ERR_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (!host_buf || bytes < (int64_t)sizeof(PlanImage)) return set_error(FSPARSE_ERR_ARG, "no plan image");
+    PlanImage h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (std::memcmp(h.magic, "FSPPLAN1", 8) != 0) return set_error(FSPARSE_ERR_ARG, "not a plan image");
+    const bool sane = h.len >= 0 && h.len <= kMaxLen && h.m >= 0 && h.n >= 0 && h.m <= INT32_MAX &&
+                      h.n <= INT32_MAX && h.nnz >= 0 && h.nnz <= h.len && h.cap >= h.nnz &&
+                      h.cap <= std::max<int64_t>(kMaxLen, h.len) &&
+                      h.nchunks == (h.len + kChunk - 1) / kChunk &&
+                      (h.numeric_tile == 1024 || h.numeric_tile == 2048 || h.numeric_tile == 4096);
+    if (!sane || bytes != image_bytes(h)) return set_error(FSPARSE_ERR_ARG, "inconsistent plan image");
+    cudaStream_t s = as_stream(stream);
+    int dev = 0;
+    FSP_CUDA(cudaGetDevice(&dev));
+    fsparse_status e;
+    if ((e = ensure_pool(dev)) != FSPARSE_OK) return e;
+    Plan *plan = new (std::nothrow) Plan();
+    if (!plan) return set_error(FSPARSE_ERR_NOMEM, "host allocation");
+    plan->device = dev;
+    plan->m = (int32_t)h.m;
+    plan->n = (int32_t)h.n;
+    plan->len = h.len;
+    plan->nnz = h.nnz;
+    plan->cap = h.cap;
+    plan->key.rb = plan->m > 0 ? bits_for((uint64_t)plan->m - 1) : 0;
+    plan->key.cb = plan->n > 0 ? bits_for((uint64_t)plan->n - 1) : 0;
+    plan->cfg = fsparse_config{h.strategy, h.radix_bits, h.sweep_items, h.sweep_threads, h.bucket_target, h.numeric_tile};
+    plan->numeric_tile = h.numeric_tile;
+    plan->nchunks = h.nchunks;
+    auto fail = [&](fsparse_status st) {
+        free_plan_arrays(*plan);
+        delete plan;
+        return st;
+    };
+    if ((e = device_alloc(reinterpret_cast<void **>(&plan->irank), (size_t)std::max<int64_t>(h.len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->perm), (size_t)std::max<int64_t>(h.len, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->irS), (size_t)std::max<int64_t>(h.cap, 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->jcS), ((size_t)h.n + 1) * 4, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&plan->chunk_slot0), ((size_t)h.nchunks + 1) * 4, s)))
+        return fail(e);
+    const char *in = static_cast<const char *>(host_buf) + sizeof(h);
+    auto put = [&](void *dst, int64_t count) {
+        const cudaError_t ce = count > 0 ? cudaMemcpyAsync(dst, in, (size_t)count * 4, cudaMemcpyHostToDevice, s)
+                                         : cudaSuccess;
+        in += (size_t)count * 4;
+        return ce;
+    };
+    cudaError_t ce = put(plan->perm, h.len);
+    if (ce == cudaSuccess) ce = put(plan->chunk_slot0, h.nchunks + 1);
+    if (ce == cudaSuccess) ce = put(plan->jcS, h.n + 1);
+    if (ce == cudaSuccess) ce = put(plan->irS, h.cap);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);   // the caller's buffer may go away
+    if (ce != cudaSuccess) return fail(cuda_error(ce, "cudaMemcpyAsync (plan import)"));
+    *plan_out = reinterpret_cast<fsparse_plan>(plan);
+    return FSPARSE_OK;
 }
 
 // ---- phase timing ------------------------------------------------------------

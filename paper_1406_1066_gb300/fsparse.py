@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         "fsparse_assemble": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_symbolic_f64": [_P, _P, _I64, _I32, _I32, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_plan_append": [_P, _P, _P, _I64, _P, ctypes.POINTER(_P)],
+        "fsparse_plan_export": [_P, _P, _I64, ctypes.POINTER(_I64)],
+        "fsparse_plan_import": [_P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_assemble_f64": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_batch_create": [_I32, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)],
         "fsparse_batch_info": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
@@ -154,6 +156,20 @@ def fsparse_assemble(ii: int, jj: int, sr: int, length: int, m: int, n: int, nzm
     if st != OK and out.value:
         lib().fsparse_plan_destroy(out.value)
     _check(st, "fsparse_assemble")
+    return out.value
+
+
+def fsparse_plan_export(plan: int) -> bytes:
+    size = _I64()
+    _check(lib().fsparse_plan_export(plan, None, 0, ctypes.byref(size)), "fsparse_plan_export")
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib().fsparse_plan_export(plan, buf, size.value, ctypes.byref(size)), "fsparse_plan_export")
+    return buf.raw
+
+
+def fsparse_plan_import(image: bytes, stream: int) -> int:
+    out = _P()
+    _check(lib().fsparse_plan_import(image, len(image), stream, ctypes.byref(out)), "fsparse_plan_import")
     return out.value
 
 
@@ -316,6 +332,10 @@ class Plan:
     def numeric(self, s, out=None):
         return numeric(self, s, out)
 
+    def export(self) -> bytes:
+        """Host image of the plan (checkpoint); see ``import_plan``."""
+        return fsparse_plan_export(self.handle)
+
     def close(self) -> None:
         if self.handle:
             fsparse_plan_destroy(self.handle)
@@ -360,6 +380,15 @@ def append(plan: Plan, ii, jj) -> Plan:
     with torch.cuda.device(plan.device):
         h = fsparse_plan_append(plan.handle, ii.data_ptr(), jj.data_ptr(), ii.numel(), _stream())
     return Plan(h, plan.device)
+
+
+def import_plan(image: bytes, device=None) -> Plan:
+    """Rebuild a plan from ``Plan.export()`` on the current (or given) device."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        h = fsparse_plan_import(image, _stream())
+    return Plan(h, dev)
 
 
 def numeric(plan: Plan, s, out=None):

@@ -86,6 +86,12 @@ def test_argument_errors_without_device(lib):
     assert lib.fsparse_symbolic_f64(None, None, 0, 0, 0, 0, None, None) == fsparse.ERR_ARG
     assert lib.fsparse_assemble_f64(None, None, None, 0, 0, 0, 0, None, 0, None, None) == fsparse.ERR_ARG
     assert lib.fsparse_plan_append(None, None, None, 0, None, None) == fsparse.ERR_ARG
+    # plan images are checked before any device access
+    assert lib.fsparse_plan_export(None, None, 0, ctypes.byref(fsparse._I64())) == fsparse.ERR_ARG
+    out = fsparse._P()
+    for image in (b"", b"x" * 200, b"FSPPLAN1" + b"\0" * 120, b"FSPPLAN1" + b"\xff" * 120):
+        assert lib.fsparse_plan_import(image, len(image), None, ctypes.byref(out)) == fsparse.ERR_ARG
+    assert lib.fsparse_plan_import(None, 0, None, None) == fsparse.ERR_ARG
     assert lib.fsparse_plan_append(None, None, None, 0, None, ctypes.byref(fsparse._P())) == fsparse.ERR_ARG
     assert lib.fsparse_assemble_f64(8, 8, None, 4, 3, 3, 0, None, 0, None,
                                     ctypes.byref(fsparse._P())) == fsparse.ERR_ARG   # NULL values
