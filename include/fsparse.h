@@ -229,15 +229,19 @@ fsparse_status fsparse_batch_destroy(fsparse_batch batch);
  * strategy: FSPARSE_SORT_ONESWEEP = global stable LSD radix sort of the
  * packed (column,row) keys, one kernel per digit with decoupled look-back;
  * FSPARSE_SORT_BUCKET = one stable partition by the high column bits,
- * then a shared-memory sort of each column bucket fused with run detection,
- * jcS, irank and the value fold.  Both give bit-identical results.  A
- * bucket that outgrows shared memory makes the library redo the call with
- * ONESWEEP (same results, more time).
+ * then one shared-memory pass per column bucket fused with run detection,
+ * jcS and the chunk slot bases.  Inside a bucket whose (column, dense row
+ * rank) key space fits a 65,536-bit map the unique keys are counted in that
+ * bitmap (no sort pass); other buckets take 8-bit radix passes.
+ * FSPARSE_SORT_BUCKET_RADIX = the same with the radix passes in every bucket.
+ * All give bit-identical results.  A bucket that outgrows shared memory
+ * makes the library redo the call with ONESWEEP (same results, more time).
  * ---------------------------------------------------------------------- */
 typedef enum fsparse_strategy {
     FSPARSE_SORT_AUTO = 0,
     FSPARSE_SORT_ONESWEEP = 1,
-    FSPARSE_SORT_BUCKET = 2
+    FSPARSE_SORT_BUCKET = 2,
+    FSPARSE_SORT_BUCKET_RADIX = 3
 } fsparse_strategy;
 
 typedef struct fsparse_config {

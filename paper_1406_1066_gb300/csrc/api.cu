@@ -232,7 +232,8 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     *folded = false;
     fsparse_status e;
     bool unfit = true;
-    if (cfg.strategy == FSPARSE_SORT_BUCKET && bucket_supported(len, plan.n, plan.key, cfg)) {
+    const bool bucket = cfg.strategy == FSPARSE_SORT_BUCKET || cfg.strategy == FSPARSE_SORT_BUCKET_RADIX;
+    if (bucket && bucket_supported(len, plan.n, plan.key, cfg)) {
         e = bucket_symbolic(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s, &unfit);
         if (e != FSPARSE_OK) return e;
     }

@@ -41,6 +41,7 @@ constexpr int64_t kMaxBuckets = 32768;
 constexpr int kMaxColBits = 12;     // 2^cs column counters in shared memory
 constexpr int kRunSortMax = 128;    // longest run put back into k order in the bucket kernel
 constexpr int kRowBits = 1 << 16;   // row ranges up to this are compressed to dense ranks
+constexpr int kKeyBits = 1 << 16;   // (column, row rank) key spaces up to this are counted in a bitmap
 
 struct BucketShape {
     int cs = 0;        // low column bits kept inside a bucket
@@ -168,6 +169,7 @@ struct BucketEmitArgs {
     uint32_t *look;
     uint32_t *ticket;
     DevStatus *st;
+    int bitmap;   // allow the bitmap counting path (else always the radix passes)
 };
 
 template <int THREADS, int IPT>
@@ -268,9 +270,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
     // which shortens the sort key; otherwise row - row_lo is used as is.
     const bool dense = range > 0 && range <= (uint32_t)kRowBits;
     int rbits;
+    uint32_t distinct = 0;
+    const int RW = (int)((range + 31) / 32);   // row bitmap words the row offsets can reach
     if (dense) {
         constexpr int WORDS = kRowBits / 32, WPT = WORDS / THREADS;
-        for (int w = tid; w < WORDS; w += THREADS) s_bits[w] = 0;
+        for (int w = tid; w < RW; w += THREADS) s_bits[w] = 0;
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
@@ -280,21 +284,198 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             }
         }
         __syncthreads();
-        uint32_t c = 0;
+        uint32_t cw[WPT], c = 0;
 #pragma unroll
-        for (int j = 0; j < WPT; ++j) c += __popc(s_bits[tid * WPT + j]);
-        uint32_t distinct;
+        for (int j = 0; j < WPT; ++j) {
+            cw[j] = tid * WPT + j < RW ? __popc(s_bits[tid * WPT + j]) : 0u;
+            c += cw[j];
+        }
         uint32_t run = block_exclusive_scan<THREADS>(c, s_scan, &distinct);
 #pragma unroll
         for (int j = 0; j < WPT; ++j) {
-            s_pref[tid * WPT + j] = (uint16_t)run;
-            run += __popc(s_bits[tid * WPT + j]);
+            if (tid * WPT + j < RW) s_pref[tid * WPT + j] = (uint16_t)run;
+            run += cw[j];
         }
         __syncthreads();
         rbits = bits_of(distinct - 1);
     } else {
         rbits = bits_of(range ? range - 1 : 0u);
     }
+    // Bitmap counting path.  With the rows ranked densely, the bucket's keys
+    // (column, row rank) span ncols * distinct values; when that fits a
+    // bitmap, the set bits ARE the bucket's unique (i,j) pairs in CCS order,
+    // and a prefix popcount over the bitmap numbers the slots: Part 3's
+    // uniqueness test and Part 4's column counts with no sort pass at all.
+    // Triplets are then grouped by slot with one counting scatter, and put
+    // into ascending k inside each run as in the radix path.
+    if (a.bitmap && dense && (uint32_t)ncols * distinct <= (uint32_t)kKeyBits) {
+        const uint32_t R = distinct, K = (uint32_t)ncols * distinct;
+        const int KW = (int)((K + 31) / 32);
+        const uint32_t rbm = (uint32_t)((1ull << rb) - 1);
+        uint32_t *s_kb = reinterpret_cast<uint32_t *>(smem + S::off_b);                 // [KW] key bitmap
+        uint16_t *s_kpref = reinterpret_cast<uint16_t *>(smem + S::off_b + kKeyBits / 8); // [KW] set bits before
+        uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem);   // [U] run sizes, until the scan
+        uint32_t *s_k = s_cnt;                                  // [nx] k, grouped by slot, after it
+        uint16_t *s_slot = reinterpret_cast<uint16_t *>(smem + (size_t)CAP * 4);   // [nx] slot of a position
+        uint16_t *s_roff = reinterpret_cast<uint16_t *>(smem + (size_t)CAP * 6);   // [U] row offset of a slot
+        uint16_t *s_lo = s_hpos;                                // [U+1] first position of each run
+        static_assert(S::bytes_b >= kKeyBits / 8 + kKeyBits / 32 * 2, "key bitmap region");
+        static_assert(CAP <= 8192, "slots and positions are packed in 13 bits");
+        for (int w = tid; w < KW; w += THREADS) s_kb[w] = 0;
+        for (int q = tid; q < nx; q += THREADS) s_cnt[q] = 0;
+        __syncthreads();
+        // Keys into the bitmap; the word becomes k (bits 0-29) | key (30-45) |
+        // row offset (46-61), or ~0 for no triplet.
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint64_t w = pk[i];
+            pk[i] = ~0ull;
+            if (valid[i]) {
+                const uint32_t roff = ((uint32_t)(w >> kb) & rbm) - row_lo;
+                const uint32_t rank = s_pref[roff >> 5] + __popc(s_bits[roff >> 5] & ((1u << (roff & 31)) - 1u));
+                const uint32_t kk = (uint32_t)(w >> (kb + rb)) * R + rank;
+                if (in_range(kk, K, a.st)) {
+                    atomicOr(&s_kb[kk >> 5], 1u << (kk & 31));
+                    pk[i] = (w & kmask) | ((uint64_t)kk << 30) | ((uint64_t)roff << 46);
+                }
+            }
+        }
+        __syncthreads();
+        // Prefix popcount of the bitmap: slot of every key, U = unique keys.
+        uint32_t U;
+        {
+            constexpr int WPT = (kKeyBits / 32 + THREADS - 1) / THREADS;
+            uint32_t c[WPT], sum = 0;
+#pragma unroll
+            for (int j = 0; j < WPT; ++j) {
+                const int w = tid * WPT + j;
+                c[j] = w < KW ? __popc(s_kb[w]) : 0u;
+                sum += c[j];
+            }
+            uint32_t run = block_exclusive_scan<THREADS>(sum, s_scan, &U);
+#pragma unroll
+            for (int j = 0; j < WPT; ++j) {
+                const int w = tid * WPT + j;
+                if (w < KW) s_kpref[w] = (uint16_t)run;
+                run += c[j];
+            }
+        }
+        if (tid == 0) st_release(a.look + x, (x == 0 ? kFlagInc : kFlagAgg) | U);
+        __syncthreads();
+        // Run sizes; every triplet takes a provisional place inside its run.
+        // The word becomes k (bits 0-29) | slot (30-42) | place (43-55).
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const uint64_t w = pk[i];
+            if (w != ~0ull) {
+                const uint32_t kk = (uint32_t)(w >> 30) & 0xffffu;
+                const uint32_t slot = s_kpref[kk >> 5] + __popc(s_kb[kk >> 5] & ((1u << (kk & 31)) - 1u));
+                if (in_range(slot, nx, a.st)) {
+                    const uint32_t place = atomicAdd(&s_cnt[slot], 1u);
+                    s_roff[slot] = (uint16_t)(w >> 46);   // the same value from every triplet of the slot
+                    pk[i] = (w & kmask) | ((uint64_t)slot << 30) | ((uint64_t)place << 43);
+                } else {
+                    pk[i] = ~0ull;
+                }
+            }
+        }
+        __syncthreads();
+        // First position of every run: exclusive scan of the run sizes.
+        {
+            uint32_t c[IPT], sum = 0;
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int r = tid * IPT + j;
+                c[j] = r < (int)U ? s_cnt[r] : 0u;
+                sum += c[j];
+            }
+            uint32_t tot;
+            uint32_t run = block_exclusive_scan<THREADS>(sum, s_scan, &tot);
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int r = tid * IPT + j;
+                if (r < (int)U) s_lo[r] = (uint16_t)run;
+                run += c[j];
+            }
+            if (tid == 0) s_lo[U] = (uint16_t)nx;
+        }
+        __syncthreads();
+        // Group the triplets by slot.
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            if (pk[i] != ~0ull) {
+                const uint32_t slot = (uint32_t)(pk[i] >> 30) & 0x1fffu;
+                const uint32_t q = s_lo[slot] + (uint32_t)(pk[i] >> 43);
+                if (in_range(q, nx, a.st)) {
+                    s_k[q] = (uint32_t)(pk[i] & kmask);
+                    s_slot[q] = (uint16_t)slot;
+                }
+            }
+        }
+        __syncthreads();
+        // Slot base: warp 0 looks back over earlier buckets while the other
+        // warps write perm; everything that needs it is written afterwards.
+        if (warp == 0) {
+            uint32_t e = 0;
+            if (x > 0) {
+                e = warp_lookback_exclusive(a.look, 1, x, a.st);
+                if (lane == 0) st_release(a.look + x, kFlagInc | (e + U));
+            }
+            if (lane == 0) s_misc[3] = e;
+        }
+        // Outputs, position by position (warp-striped, so the lanes of a warp
+        // mostly share a run): each triplet lands at lo + (number of triplets
+        // of its run with a smaller k); the first carries the head bit.  The
+        // chunk slot bases of chunks starting here are kept, bucket-local.
+        uint16_t *s_cs = reinterpret_cast<uint16_t *>(s_bits);   // row bitmap no longer needed
+        const int64_t c_first = (b0 + kChunk - 1) >> kChunkShift;
+#pragma unroll
+        for (int i = 0; i < IPT; ++i) {
+            const int q = warp * 32 * IPT + i * 32 + lane;
+            if (q >= nx) continue;
+            const uint32_t kq = s_k[q], slot = s_slot[q];
+            if (!in_range(slot, U, a.st)) continue;
+            const int lo = s_lo[slot], hi = s_lo[slot + 1];
+            int dest = q;
+            if (hi - lo > 1) {
+                if (hi - lo > kRunSortMax) {
+                    atomicOr(&a.st->overflow, 1u);   // redone by the onesweep path
+                } else {
+                    int rank = 0, r = lo;
+                    for (; r < hi && (r & 3); ++r) rank += s_k[r] < kq;
+                    for (; r + 4 <= hi; r += 4) {
+                        const uint4 f = *reinterpret_cast<const uint4 *>(s_k + r);
+                        rank += (f.x < kq) + (f.y < kq) + (f.z < kq) + (f.w < kq);
+                    }
+                    for (; r < hi; ++r) rank += s_k[r] < kq;
+                    dest = lo + rank;
+                }
+            }
+            const int64_t gp = b0 + dest;
+            const bool head = dest == lo;
+            a.perm[gp] = kq | (head ? kHeadBit : 0u);
+            if ((gp & (kChunk - 1)) == 0 && in_range((gp >> kChunkShift) - c_first, kMaxBucketCap / kChunk + 1, a.st))
+                s_cs[(gp >> kChunkShift) - c_first] = (uint16_t)(head ? slot : slot + 1);
+        }
+        __syncthreads();
+        const uint32_t E = s_misc[3];
+        for (int r = tid; r < (int)U; r += THREADS)
+            if (in_range(E + r, a.len, a.st)) a.irS[E + r] = (int32_t)(s_roff[r] + row_lo);
+        const int64_t c_end = (b0 + nx + kChunk - 1) >> kChunkShift;   // chunks starting in [b0, b0+nx)
+        for (int64_t c = c_first + tid; c < c_end; c += THREADS) a.chunk_slot0[c] = E + s_cs[c - c_first];
+        // jcS: E + number of unique keys before each column's first key c*R.
+        for (int c = tid; c < ncols; c += THREADS) {
+            const uint32_t bpos = (uint32_t)c * R;
+            a.jcS[col0 + c] = (int32_t)(E + s_kpref[bpos >> 5] + __popc(s_kb[bpos >> 5] & ((1u << (bpos & 31)) - 1u)));
+        }
+        if (x == a.nb - 1 && tid == 0) {
+            a.jcS[a.n] = (int32_t)(E + U);
+            a.st->nnz = E + U;
+            a.chunk_slot0[a.nchunks] = E + U;
+        }
+        return;
+    }
+
     const int npass = (a.cs + rbits + 7) / 8;
     // When a row rank replaces the row, the row offset (< 2^16) rides along
     // in the bits above the sorted digits, so the output needs no search.
@@ -449,7 +630,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                 } else {
                     row = (uint32_t)(sk & rmaskx);
                     if (dense) {   // row of dense rank `row`: word by binary search, bit by __fns
-                        int wlo = 0, whi = kRowBits / 32 - 1;
+                        int wlo = 0, whi = RW - 1;
                         while (wlo < whi) {
                             const int mid = (wlo + whi + 1) >> 1;
                             if (s_pref[mid] <= row) wlo = mid; else whi = mid - 1;
@@ -526,6 +707,18 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         (e = scratch.get(&dmax, 1)) || (e = scratch.get(&tot, (size_t)kMaxBuckets)) ||
         (e = scratch.get(&bstart, (size_t)kMaxBuckets + 1)) || (e = scratch.get(&words, (size_t)len)))
         return e;
+    // The largest bucket comes back through a pinned word, so the scan and
+    // the scatter for the current width are queued before the host waits:
+    // the GPU does not idle across the read (they are redone if the width
+    // has to shrink).
+    static thread_local uint32_t *h_largest = nullptr;
+    if (!h_largest) FSP_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_largest), sizeof(uint32_t)));
+    cudaEvent_t got_largest = nullptr;
+    FSP_CUDA(cudaEventCreateWithFlags(&got_largest, cudaEventDisableTiming));
+    struct EventGuard {
+        cudaEvent_t e;
+        ~EventGuard() { cudaEventDestroy(e); }
+    } guard{got_largest};
     int G = 1, nb = 0;
     uint32_t largest = 0;
     for (int attempt = 0;; ++attempt) {
@@ -543,8 +736,19 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         FSP_CUDA(cudaMemsetAsync(dmax, 0, 4, s));
         bucket_max_kernel<<<std::min((nb + 255) / 256, 4 * sm_count(0)), 256, 0, s>>>(tot, nb, dmax);
         FSP_LAUNCHED();
-        FSP_CUDA(cudaMemcpyAsync(&largest, dmax, 4, cudaMemcpyDeviceToHost, s));
-        FSP_CUDA(cudaStreamSynchronize(s));
+        FSP_CUDA(cudaMemcpyAsync(h_largest, dmax, 4, cudaMemcpyDeviceToHost, s));
+        FSP_CUDA(cudaEventRecord(got_largest, s));
+        phase_mark("bucket_count");
+        FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)nb + 1) * 4, s));
+        FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
+        if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
+        FSP_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
+        bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
+                                                     words, st);
+        FSP_LAUNCHED();
+        phase_mark("bucket_scatter");
+        FSP_CUDA(cudaEventSynchronize(got_largest));
+        largest = *h_largest;
         if (largest <= (uint32_t)kMaxBucketCap) break;
         if (sh.cs == 0 || attempt >= 3) {   // a column (or a few) beyond the cap: onesweep instead
             *unfit = true;
@@ -560,16 +764,6 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         }
     }
     sh.grid = G;
-    phase_mark("bucket_count");
-    FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)nb + 1) * 4, s));
-    FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
-    if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
-    const size_t table = (size_t)nb * 4;
-    FSP_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
-    bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
-                                                 words, st);
-    FSP_LAUNCHED();
-    phase_mark("bucket_scatter");
 
     BucketEmitArgs a{};
     a.words = words;
@@ -588,6 +782,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     a.look = look;
     a.ticket = ticket;
     a.st = st;
+    a.bitmap = cfg.strategy != FSPARSE_SORT_BUCKET_RADIX;
     if (largest <= (uint32_t)kEmitCap[0]) e = run_emit<256, 16>(a, nb, s);
     else if (largest <= (uint32_t)kEmitCap[1]) e = run_emit<512, 12>(a, nb, s);
     else e = run_emit<512, 16>(a, nb, s);

@@ -29,7 +29,7 @@ bool config_valid(const fsparse_config &c) {
     const bool items = c.sweep_items == 8 || c.sweep_items == 12 || c.sweep_items == 16;
     const bool threads = c.sweep_threads == 256 || c.sweep_threads == 512;
     const bool tile = c.numeric_tile == 1024 || c.numeric_tile == 2048 || c.numeric_tile == 4096;
-    return c.strategy >= 0 && c.strategy <= 2 && c.radix_bits >= 6 && c.radix_bits <= 8 && items &&
+    return c.strategy >= 0 && c.strategy <= 3 && c.radix_bits >= 6 && c.radix_bits <= 8 && items &&
            threads && c.bucket_target >= 1024 && c.bucket_target <= 16384 && tile;
 }
 
@@ -80,10 +80,11 @@ std::vector<fsparse_config> tune_candidates(int64_t len, const KeyLayout &key) {
     for (int r = 6; r <= 8; ++r)
         for (int th : {256, 512})
             for (int it : {8, 12, 16}) out.push_back(fsparse_config{FSPARSE_SORT_ONESWEEP, r, it, th, 8192, tile});
-    for (int bt : {2048, 4096, 8192, 12288}) {
-        fsparse_config c{FSPARSE_SORT_BUCKET, 8, 16, 256, bt, tile};
-        if (bucket_supported(len, 1 << key.cb, key, c)) out.push_back(c);
-    }
+    for (int strat : {FSPARSE_SORT_BUCKET, FSPARSE_SORT_BUCKET_RADIX})
+        for (int bt : {2048, 4096, 8192, 12288}) {
+            fsparse_config c{strat, 8, 16, 256, bt, tile};
+            if (bucket_supported(len, 1 << key.cb, key, c)) out.push_back(c);
+        }
     return out;
 }
 

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfsparse.so")
 
 OK, ERR_ARG, ERR_INDEX, ERR_NZMAX, ERR_SIZE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL = range(9)
-SORT_AUTO, SORT_ONESWEEP, SORT_BUCKET = 0, 1, 2
+SORT_AUTO, SORT_ONESWEEP, SORT_BUCKET, SORT_BUCKET_RADIX = 0, 1, 2, 3
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_INDEX", "ERR_NZMAX", "ERR_SIZE", "ERR_NOMEM", "ERR_CUDA",
                 "ERR_TIMEOUT", "ERR_INTERNAL"]
 

@@ -2,7 +2,9 @@
 oracle.  Inputs with exactly c triplets per column make the bucket sizes
 known: the width rule puts 2^cs columns in a bucket with c * 2^cs in
 (target / 2, target], so the largest bucket lands in a chosen capacity class
-(4096 -> 256 x 16, 6144 -> 512 x 12, 8192 -> 512 x 16)."""
+(4096 -> 256 x 16, 6144 -> 512 x 12, 8192 -> 512 x 16).  Strategy 2 counts a
+bucket's keys in a bitmap when its (column, row rank) space fits 2^16 bits,
+strategy 3 always takes the radix passes."""
 import numpy as np
 import pytest
 
@@ -22,22 +24,24 @@ def per_column(n_cols, c, m, seed, used_cols=None):
     return ii, jj, s
 
 
+@pytest.mark.parametrize("strategy", [2, 3])
 @pytest.mark.parametrize("c,target", [(32, 4096), (40, 8192), (100, 8192)],
                          ids=["bucket_4096_256x16", "bucket_5120_512x12", "bucket_6400_512x16"])
-def test_bucket_shape(c, target):
+def test_bucket_shape(c, target, strategy):
     n, m = 1 << 14, 5000
     ii, jj, s = per_column(n, c, m, 61 + c)
-    with config(strategy=2, bucket_target=target):
+    with config(strategy=strategy, bucket_target=target):
         g = gpu_assemble(ii, jj, s, m, n)
     assert_same(g, oracle.assemble(ii, jj, s, m, n))
 
 
-def test_uneven_columns_narrow_the_buckets():
+@pytest.mark.parametrize("strategy", [2, 3])
+def test_uneven_columns_narrow_the_buckets(strategy):
     """Half the columns empty: the average suggests 6400 per bucket, the real
     largest is 12800, so the buckets are halved before the scatter."""
     n, m = 1 << 14, 5000
     ii, jj, s = per_column(n, 100, m, 62, used_cols=n // 2)
-    with config(strategy=2, bucket_target=8192):
+    with config(strategy=strategy, bucket_target=8192):
         g = gpu_assemble(ii, jj, s, m, n)
     assert_same(g, oracle.assemble(ii, jj, s, m, n))
 
@@ -48,6 +52,19 @@ def test_three_pass_rows_without_stash_room():
     not fit above the digits and rows are recovered from the rank bitmap."""
     n, m = 1 << 19, 60000
     ii, jj, s = per_column(n, 40, m, 63)
+    with config(strategy=2, bucket_target=8192):
+        g = gpu_assemble(ii, jj, s, m, n)
+    assert_same(g, oracle.assemble(ii, jj, s, m, n))
+
+
+@pytest.mark.parametrize("m", [1024, 1100, 600])
+def test_key_bitmap_capacity(m):
+    """64 columns x 100 triplets per bucket with rows drawn from [1, m]: every
+    bucket sees about min(m, 6400) distinct rows, so its key space is 64 * 1024
+    = 2^16 bits exactly (bitmap), 64 * ~1100 (radix passes) or 64 * 600
+    (bitmap, with many repeated (i,j) pairs).  Each bucket decides for itself."""
+    n = 1 << 14
+    ii, jj, s = per_column(n, 100, m, 64 + m)
     with config(strategy=2, bucket_target=8192):
         g = gpu_assemble(ii, jj, s, m, n)
     assert_same(g, oracle.assemble(ii, jj, s, m, n))

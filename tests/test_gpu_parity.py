@@ -11,10 +11,10 @@ from paper_1406_1066_gb300 import fsparse, inputs
 
 pytestmark = pytest.mark.gpu
 
-STRATEGIES = [fsparse.SORT_ONESWEEP, fsparse.SORT_BUCKET]
+STRATEGIES = [fsparse.SORT_ONESWEEP, fsparse.SORT_BUCKET, fsparse.SORT_BUCKET_RADIX]
 
 
-@pytest.fixture(params=STRATEGIES, ids=["onesweep", "bucket"])
+@pytest.fixture(params=STRATEGIES, ids=["onesweep", "bucket", "bucket_radix"])
 def strategy(request):
     with config(strategy=request.param):
         yield request.param
