@@ -14,17 +14,22 @@
 //   3. scatter:  every block re-reads its slice of ii/jj and appends packed
 //                words  (j-1 low bits | i-1 | k)  to its ranges -- one 8-byte
 //                write per triplet, the only global reordering pass;
-//   4. emit:     one CTA per bucket (taken by atomic ticket) loads the bucket,
-//                compresses the row range, sorts (column, row) with a stable
-//                LSD radix sort in shared memory (rank.cuh), detects runs by
-//                comparing neighbours (the collision detection of Part 3),
-//                numbers the slots with one decoupled look-back across
-//                buckets, and writes perm -- each run in ascending k, since
-//                the scatter keeps no order inside a block: every triplet
-//                counts the triplets of its run with a smaller k and lands
-//                that far into the run --, irS, jcS (Part 4's prefix, per
-//                bucket column) and the numeric chunk slot bases (the values
-//                are folded by the numeric kernel afterwards).
+//   4. emit:     one CTA per bucket (taken by atomic ticket) loads the bucket
+//                and ranks its rows densely.  When the (column, row rank)
+//                key space fits a 2^16-bit map, every triplet sets its key's
+//                bit: the set bits are the bucket's unique (i,j) pairs in CCS
+//                order (the collision detection of Part 3), a prefix
+//                popcount numbers them and counts each column (Part 4), and
+//                one counting scatter groups the triplets by slot.  Other
+//                buckets sort (column, row) with a stable LSD radix sort in
+//                shared memory (rank.cuh) and detect runs by comparing
+//                neighbours.  Either way the slots are numbered across
+//                buckets with one decoupled look-back, and the kernel writes
+//                perm -- each run in ascending k, since the scatter keeps no
+//                order inside a block: every triplet counts the triplets of
+//                its run with a smaller k and lands that far into the run --,
+//                irS, jcS and the numeric chunk slot bases (the values are
+//                folded by the numeric kernel afterwards).
 //
 // A bucket above the kernel's capacity, or a run longer than kRunSortMax,
 // sets DevStatus::overflow; the host then redoes the call with the global
