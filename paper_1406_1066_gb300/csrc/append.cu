@@ -7,9 +7,9 @@
 // triplet numbers continuing at len1.  Both plans are already sorted by
 // (column, row) with runs in ascending k, so the new plan is a merge:
 //
-//   * slot keys: key(s) = column << 32 | row for every CCS slot of each plan;
-//   * ranks by a merge path over the two sorted key lists: for every slot of
-//     one plan, the number of keys of the other plan below it and whether the
+//   * ranks by a merge of the two plans' sorted rows, column by column (the
+//     columns are aligned, so no search is needed): for every slot of one
+//     plan, the number of keys of the other plan below it and whether the
 //     other plan holds the same key;
 //   * merged slot of an old slot a = a + (new keys below it) - (shared keys
 //     before it); of a new slot b = b + (old keys below it) - (shared keys
@@ -27,61 +27,73 @@
 
 namespace fsp {
 
+// The kChunk perm entries of chunk q (128-bit loads when the chunk is whole
+// and aligned; entries past len read as 0).
+__device__ __forceinline__ void load_chunk(const uint32_t *__restrict__ perm, int64_t len, int64_t q,
+                                           uint32_t (&pm)[kChunk]) {
+    const int64_t p0 = q * kChunk;
+    if (p0 + kChunk <= len && (reinterpret_cast<uintptr_t>(perm) & 15) == 0) {
+#pragma unroll
+        for (int v = 0; v < kChunk / 4; ++v) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(perm + p0) + v);
+            pm[4 * v] = x.x;
+            pm[4 * v + 1] = x.y;
+            pm[4 * v + 2] = x.z;
+            pm[4 * v + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kChunk; ++i) pm[i] = p0 + i < len ? __ldg(perm + p0 + i) : 0u;
+    }
+}
+
 // First position of every run: rs[slot] = p at run heads, rs[nnz] = len.
 __global__ void run_starts_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ chunk_slot0,
                                   int64_t len, int64_t nchunks, uint32_t *__restrict__ rs) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunks;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p0 = q * kChunk, p1 = min64(p0 + kChunk, len);
+        const int64_t p0 = q * kChunk;
+        uint32_t pm[kChunk];
+        load_chunk(perm, len, q, pm);
         uint32_t slot = chunk_slot0[q];   // runs before the chunk = index of the next run
-        for (int64_t p = p0; p < p1; ++p)
-            if (perm[p] & kHeadBit) rs[slot++] = (uint32_t)p;
+#pragma unroll
+        for (int i = 0; i < kChunk; ++i)
+            if (p0 + i < len && (pm[i] & kHeadBit)) rs[slot++] = (uint32_t)(p0 + i);
         if (q == nchunks - 1) rs[chunk_slot0[nchunks]] = (uint32_t)len;
     }
 }
 
-// key(s) = column << 32 | row, one thread per column writing its slots.
-__global__ void slot_keys_kernel(const int32_t *__restrict__ jcS, int32_t n, const int32_t *__restrict__ irS,
-                                 uint64_t *__restrict__ keys) {
+// Ranks across the two plans, one thread per column: the column's old rows
+// irA[jcA[c] .. jcA[c+1]) and new rows irB[jcB[c] .. jcB[c+1]) are both
+// ascending, so one merge gives, for an old slot x, lbA[x] = new slots with
+// a smaller key (all new slots of earlier columns plus the smaller rows of
+// this one) and eqA[x] = the new plan holds the same key; and for a new slot
+// y, lbB[y] = old slots with a smaller key and eqB[y] likewise.
+__global__ void merge_columns_kernel(const int32_t *__restrict__ jcA, const int32_t *__restrict__ irA,
+                                     const int32_t *__restrict__ jcB, const int32_t *__restrict__ irB, int32_t n,
+                                     uint32_t *__restrict__ lbA, uint32_t *__restrict__ eqA,
+                                     uint32_t *__restrict__ lbB, uint32_t *__restrict__ eqB) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s0 = jcS[c], s1 = jcS[c + 1];
-        for (int32_t s = s0; s < s1; ++s) keys[s] = ((uint64_t)(uint32_t)c << 32) | (uint32_t)irS[s];
-    }
-}
-
-// Merge path over the two sorted key lists (old keys first on ties): thread t
-// finds where merged position 8t falls by one binary search, then merges 8
-// steps.  An old key met at merged position i + j (i old, j new before it)
-// has lbA = j new keys below it; a new key has i old keys not above it, eqB
-// telling whether the last of them is equal, and lbB = i - eqB.
-constexpr int kMergeSteps = 8;
-
-__global__ void merge_path_kernel(const uint64_t *__restrict__ a, int64_t na, const uint64_t *__restrict__ b,
-                                  int64_t nb, uint32_t *__restrict__ lbA, uint32_t *__restrict__ eqA,
-                                  uint32_t *__restrict__ lbB, uint32_t *__restrict__ eqB) {
-    const int64_t total = na + nb;
-    const int64_t nthreads = (total + kMergeSteps - 1) / kMergeSteps;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t d = t * kMergeSteps;
-        int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
-        while (lo < hi) {   // i = old keys among the first d merged
-            const int64_t mid = (lo + hi) >> 1;
-            if (a[mid] <= b[d - mid - 1]) lo = mid + 1; else hi = mid;
-        }
-        int64_t i = lo, j = d - lo;
-        const int64_t end = min64(d + kMergeSteps, total);
-        for (int64_t step = d; step < end; ++step) {
-            if (j >= nb || (i < na && a[i] <= b[j])) {
-                lbA[i] = (uint32_t)j;
-                eqA[i] = (j < nb && b[j] == a[i]) ? 1u : 0u;
-                ++i;
-            } else {
-                const uint32_t e = (i > 0 && a[i - 1] == b[j]) ? 1u : 0u;
-                lbB[j] = (uint32_t)(i - e);
-                eqB[j] = e;
-                ++j;
+        int32_t x = jcA[c], y = jcB[c];
+        const int32_t xe = jcA[c + 1], ye = jcB[c + 1];
+        int32_t rx = x < xe ? irA[x] : 0, ry = y < ye ? irB[y] : 0;
+        while (x < xe || y < ye) {
+            if (y >= ye || (x < xe && rx < ry)) {
+                lbA[x] = (uint32_t)y;
+                eqA[x] = 0u;
+                if (++x < xe) rx = irA[x];
+            } else if (x >= xe || ry < rx) {
+                lbB[y] = (uint32_t)x;
+                eqB[y] = 0u;
+                if (++y < ye) ry = irB[y];
+            } else {   // the same (i,j) in both plans: one slot of the merge
+                lbA[x] = (uint32_t)y;
+                eqA[x] = 1u;
+                lbB[y] = (uint32_t)x;
+                eqB[y] = 1u;
+                if (++x < xe) rx = irA[x];
+                if (++y < ye) ry = irB[y];
             }
         }
     }
@@ -106,29 +118,50 @@ __global__ void merge_jcs_kernel(const int32_t *__restrict__ jc1, const int32_t 
         out[c] = (int32_t)((int64_t)jc1[c] + jc2[c] - shared1[jc1[c]]);
 }
 
-// Positions of one side's runs in the merged order.  For the old side
-// (second_side = 0) a run moves by other_rs[lb]: the new triplets with a
-// smaller key.  For the new side it moves by other_rs[lb + eq]: the old
-// triplets with a key not above its own; its head bit is dropped when the old
-// side holds the same key (the old run starts that slot).
+// Positions of one side's runs in the merged order, one thread per position
+// (a warp takes 32 consecutive positions, two chunks, so loads and stores
+// are coalesced and the lanes of one run share their lookups).  The slot of
+// a position is the run before the warp's first chunk plus the heads up to
+// it.  For the old side (second_side = 0) a run moves by other_rs[lb]: the
+// new triplets with a smaller key.  For the new side it moves by
+// other_rs[lb + eq]: the old triplets with a key not above its own; its head
+// bit is dropped when the old side holds the same key (the old run starts
+// that slot).
 __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ chunk_slot0,
-                                       int64_t len, int64_t nchunks, const uint32_t *__restrict__ lb,
+                                       int64_t len, int64_t nnz, const uint32_t *__restrict__ lb,
                                        const uint32_t *__restrict__ eq, const uint32_t *__restrict__ other_rs,
                                        int second_side, uint32_t kofs, uint32_t *__restrict__ out,
                                        int64_t len_out, DevStatus *st) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nchunks;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p0 = q * kChunk, p1 = min64(p0 + kChunk, len);
-        int64_t slot = (int64_t)chunk_slot0[q] - 1;   // run of the position before the chunk
-        for (int64_t p = p0; p < p1; ++p) {
-            const uint32_t x = perm[p];
-            bool head = (x & kHeadBit) != 0;
-            slot += head;
-            const uint32_t e = second_side ? eq[slot] : 0u;
-            const int64_t t = p + other_rs[lb[slot] + e];
-            if (second_side && e) head = false;
-            if (in_range(t, len_out, st)) out[t] = ((x & kIndexMask) + kofs) | (head ? kHeadBit : 0u);
-        }
+    const int lane = threadIdx.x & 31;
+    const uint32_t le = lanemask_lt() | (1u << lane);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < len;
+         w0 += warps * 32) {
+        const int64_t p = w0 + lane;
+        const uint32_t x = p < len ? __ldg(perm + p) : 0u;
+        const bool head = (x & kHeadBit) != 0;
+        const uint32_t hm = __ballot_sync(0xffffffffu, head);
+        const int64_t slot = (int64_t)chunk_slot0[w0 >> kChunkShift] - 1 + __popc(hm & le);
+        if (p >= len || !in_range(slot, nnz, st)) continue;
+        const uint32_t e = second_side ? eq[slot] : 0u;
+        const int64_t t = p + other_rs[lb[slot] + e];
+        const bool keep = head && !(second_side && e);
+        if (in_range(t, len_out, st)) out[t] = ((x & kIndexMask) + kofs) | (keep ? kHeadBit : 0u);
+    }
+}
+
+// Run heads per chunk of the merged order (a warp counts two chunks).
+__global__ void merged_chunk_heads_kernel(const uint32_t *__restrict__ perm, int64_t len, int64_t nchunks,
+                                          uint32_t *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < len;
+         w0 += warps * 32) {
+        const int64_t p = w0 + lane;
+        const bool head = p < len && (__ldg(perm + p) & kHeadBit) != 0;
+        const uint32_t hm = __ballot_sync(0xffffffffu, head);
+        const int64_t q = (w0 >> kChunkShift) + (lane >> 4);
+        if ((lane & 15) == 0 && q < nchunks) counts[q] = __popc(hm & (0xffffu << (lane & 16)));
     }
 }
 
@@ -149,11 +182,8 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
                             cudaStream_t s) {
     const int64_t na = a.nnz, nb = b.nnz;
     uint32_t *rsA, *rsB, *lbA, *eqA, *lbB, *eqB, *shA, *shB;
-    uint64_t *keyA, *keyB;
     fsparse_status e;
     if ((e = scratch.get(&rsA, (size_t)na + 1)) || (e = scratch.get(&rsB, (size_t)nb + 1)) ||
-        (e = scratch.get(&keyA, (size_t)std::max<int64_t>(na, 1))) ||
-        (e = scratch.get(&keyB, (size_t)std::max<int64_t>(nb, 1))) ||
         (e = scratch.get(&lbA, (size_t)na + 1)) || (e = scratch.get(&eqA, (size_t)na + 1)) ||
         (e = scratch.get(&lbB, (size_t)nb + 1)) || (e = scratch.get(&eqB, (size_t)nb + 1)) ||
         (e = scratch.get(&shA, (size_t)na + 1)) || (e = scratch.get(&shB, (size_t)nb + 1)))
@@ -171,17 +201,8 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
     } else {
         FSP_CUDA(cudaMemsetAsync(rsB, 0, 4, s));
     }
-    if (na > 0) {
-        slot_keys_kernel<<<grid_for(a.n), 256, 0, s>>>(a.jcS, a.n, a.irS, keyA);
-        FSP_LAUNCHED();
-    }
-    if (nb > 0) {
-        slot_keys_kernel<<<grid_for(b.n), 256, 0, s>>>(b.jcS, b.n, b.irS, keyB);
-        FSP_LAUNCHED();
-    }
     if (na + nb > 0) {
-        merge_path_kernel<<<grid_for((na + nb + kMergeSteps - 1) / kMergeSteps), 256, 0, s>>>(
-            keyA, na, keyB, nb, lbA, eqA, lbB, eqB);
+        merge_columns_kernel<<<grid_for(a.n), 256, 0, s>>>(a.jcS, a.irS, b.jcS, b.irS, a.n, lbA, eqA, lbB, eqB);
         FSP_LAUNCHED();
     }
     if ((e = exclusive_scan_u32(eqA, shA, na, st, scratch, s)) != FSPARSE_OK) return e;
@@ -199,20 +220,24 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
     merged_nnz_kernel<<<1, 1, 0, s>>>(na, nb, shA + na, st);
     FSP_LAUNCHED();
     if (a.len > 0) {
-        merge_positions_kernel<<<grid_for(a.nchunks), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, a.nchunks, lbA,
-                                                                   eqA, rsB, 0, 0u, out.perm, out.len, st);
+        merge_positions_kernel<<<grid_for((a.len + 7) / 8), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, na, lbA,
+                                                                        eqA, rsB, 0, 0u, out.perm, out.len, st);
         FSP_LAUNCHED();
     }
     if (b.len > 0) {
-        merge_positions_kernel<<<grid_for(b.nchunks), 256, 0, s>>>(b.perm, b.chunk_slot0, b.len, b.nchunks, lbB,
-                                                                   eqB, rsA, 1, (uint32_t)a.len, out.perm,
-                                                                   out.len, st);
+        merge_positions_kernel<<<grid_for((b.len + 7) / 8), 256, 0, s>>>(b.perm, b.chunk_slot0, b.len, nb, lbB,
+                                                                        eqB, rsA, 1, (uint32_t)a.len, out.perm,
+                                                                        out.len, st);
         FSP_LAUNCHED();
     }
     // chunk slot bases of the merged order; nnz = na + nb - shared
     uint32_t *counts;
     if ((e = scratch.get(&counts, (size_t)out.nchunks + 1)) != FSPARSE_OK) return e;
-    if ((e = launch_chunk_heads(out.perm, out.len, counts, out.nchunks, s)) != FSPARSE_OK) return e;
+    if (out.len > 0) {
+        merged_chunk_heads_kernel<<<grid_for((out.len + 7) / 8), 256, 0, s>>>(out.perm, out.len, out.nchunks,
+                                                                             counts);
+        FSP_LAUNCHED();
+    }
     return exclusive_scan_u32(counts, out.chunk_slot0, out.nchunks, st, scratch, s);
 }
 

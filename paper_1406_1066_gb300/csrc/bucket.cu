@@ -241,6 +241,26 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         }
         return;
     }
+    if (nx == 0) {   // empty bucket: its columns start where the previous bucket ends
+        if (warp == 0) {
+            uint32_t e = 0;
+            if (lane == 0) st_release(a.look + x, x == 0 ? kFlagInc : kFlagAgg);
+            if (x > 0) {
+                e = warp_lookback_exclusive(a.look, 1, x, a.st);
+                if (lane == 0) st_release(a.look + x, kFlagInc | e);
+            }
+            if (lane == 0) s_misc[3] = e;
+        }
+        __syncthreads();
+        const uint32_t E = s_misc[3];
+        for (int c = tid; c < ncols; c += THREADS) a.jcS[col0 + c] = (int32_t)E;
+        if (x == a.nb - 1 && tid == 0) {
+            a.jcS[a.n] = (int32_t)E;
+            a.st->nnz = E;
+            a.chunk_slot0[a.nchunks] = E;
+        }
+        return;
+    }
 
     // Load the bucket (warp-striped) and find its row range.
     uint64_t pk[IPT];
