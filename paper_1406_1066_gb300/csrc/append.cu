@@ -68,32 +68,50 @@ __global__ void run_starts_kernel(const uint32_t *__restrict__ perm, const uint3
 // ascending, so one merge gives, for an old slot x, lbA[x] = new slots with
 // a smaller key (all new slots of earlier columns plus the smaller rows of
 // this one) and eqA[x] = the new plan holds the same key; and for a new slot
-// y, lbB[y] = old slots with a smaller key and eqB[y] likewise.
-__global__ void merge_columns_kernel(const int32_t *__restrict__ jcA, const int32_t *__restrict__ irA,
-                                     const int32_t *__restrict__ jcB, const int32_t *__restrict__ irB, int32_t n,
-                                     uint32_t *__restrict__ lbA, uint32_t *__restrict__ eqA,
-                                     uint32_t *__restrict__ lbB, uint32_t *__restrict__ eqB) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int32_t x = jcA[c], y = jcB[c];
-        const int32_t xe = jcA[c + 1], ye = jcB[c + 1];
-        int32_t rx = x < xe ? irA[x] : 0, ry = y < ye ? irB[y] : 0;
+// y, lbB[y] = old slots with a smaller key and eqB[y] likewise.  Columns of
+// up to kStage rows per side are first copied to the thread's own slice of
+// shared memory with independent loads, so the merge does not wait on one
+// global load per step.
+constexpr int kStage = 16;
+constexpr int kColThreads = 128;
+
+__global__ void __launch_bounds__(kColThreads)
+    merge_columns_kernel(const int32_t *__restrict__ jcA, const int32_t *__restrict__ irA,
+                         const int32_t *__restrict__ jcB, const int32_t *__restrict__ irB, int32_t n,
+                         uint32_t *__restrict__ lbA, uint32_t *__restrict__ eqA,
+                         uint32_t *__restrict__ lbB, uint32_t *__restrict__ eqB) {
+    __shared__ int32_t s_rows[2 * kStage][kColThreads];   // [row index][thread]: conflict-free
+    const int tid = threadIdx.x;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + tid; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x0 = jcA[c], xe = jcA[c + 1], y0 = jcB[c], ye = jcB[c + 1];
+        const int32_t na = xe - x0, nb = ye - y0;
+        const bool staged = na <= kStage && nb <= kStage;
+        if (staged) {
+#pragma unroll
+            for (int u = 0; u < kStage; ++u) {
+                if (u < na) s_rows[u][tid] = __ldg(irA + x0 + u);
+                if (u < nb) s_rows[kStage + u][tid] = __ldg(irB + y0 + u);
+            }
+        }
+        int32_t x = x0, y = y0;
         while (x < xe || y < ye) {
+            const int32_t rx = x < xe ? (staged ? s_rows[x - x0][tid] : irA[x]) : 0;
+            const int32_t ry = y < ye ? (staged ? s_rows[kStage + y - y0][tid] : irB[y]) : 0;
             if (y >= ye || (x < xe && rx < ry)) {
                 lbA[x] = (uint32_t)y;
                 eqA[x] = 0u;
-                if (++x < xe) rx = irA[x];
+                ++x;
             } else if (x >= xe || ry < rx) {
                 lbB[y] = (uint32_t)x;
                 eqB[y] = 0u;
-                if (++y < ye) ry = irB[y];
+                ++y;
             } else {   // the same (i,j) in both plans: one slot of the merge
                 lbA[x] = (uint32_t)y;
                 eqA[x] = 1u;
                 lbB[y] = (uint32_t)x;
                 eqB[y] = 1u;
-                if (++x < xe) rx = irA[x];
-                if (++y < ye) ry = irB[y];
+                ++x;
+                ++y;
             }
         }
     }
@@ -126,7 +144,10 @@ __global__ void merge_jcs_kernel(const int32_t *__restrict__ jc1, const int32_t 
 // new triplets with a smaller key.  For the new side it moves by
 // other_rs[lb + eq]: the old triplets with a key not above its own; its head
 // bit is dropped when the old side holds the same key (the old run starts
-// that slot).
+// that slot).  Each warp step handles kGroups such 32-position groups, whose
+// chains of dependent lookups (perm -> slot -> lb/eq -> other_rs) overlap.
+constexpr int kGroups = 4;
+
 __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ chunk_slot0,
                                        int64_t len, int64_t nnz, const uint32_t *__restrict__ lb,
                                        const uint32_t *__restrict__ eq, const uint32_t *__restrict__ other_rs,
@@ -135,18 +156,38 @@ __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const 
     const int lane = threadIdx.x & 31;
     const uint32_t le = lanemask_lt() | (1u << lane);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < len;
-         w0 += warps * 32) {
-        const int64_t p = w0 + lane;
-        const uint32_t x = p < len ? __ldg(perm + p) : 0u;
-        const bool head = (x & kHeadBit) != 0;
-        const uint32_t hm = __ballot_sync(0xffffffffu, head);
-        const int64_t slot = (int64_t)chunk_slot0[w0 >> kChunkShift] - 1 + __popc(hm & le);
-        if (p >= len || !in_range(slot, nnz, st)) continue;
-        const uint32_t e = second_side ? eq[slot] : 0u;
-        const int64_t t = p + other_rs[lb[slot] + e];
-        const bool keep = head && !(second_side && e);
-        if (in_range(t, len_out, st)) out[t] = ((x & kIndexMask) + kofs) | (keep ? kHeadBit : 0u);
+    const int64_t span = 32 * kGroups;
+    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * span; w0 < len;
+         w0 += warps * span) {
+        uint32_t x[kGroups], base[kGroups];
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            const int64_t p = w0 + 32 * g + lane;
+            x[g] = p < len ? __ldg(perm + p) : 0u;
+            base[g] = w0 + 32 * g < len ? __ldg(chunk_slot0 + ((w0 + 32 * g) >> kChunkShift)) : 0u;
+        }
+        int64_t slot[kGroups];
+        uint32_t e[kGroups], l[kGroups];
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            const uint32_t hm = __ballot_sync(0xffffffffu, (x[g] & kHeadBit) != 0);
+            slot[g] = (int64_t)base[g] - 1 + __popc(hm & le);
+            const bool ok = w0 + 32 * g + lane < len && slot[g] >= 0 && slot[g] < nnz;
+            e[g] = ok && second_side ? __ldg(eq + slot[g]) : 0u;
+            l[g] = ok ? __ldg(lb + slot[g]) : 0u;
+            if (!ok) slot[g] = -1;
+        }
+#pragma unroll
+        for (int g = 0; g < kGroups; ++g) {
+            const int64_t p = w0 + 32 * g + lane;
+            if (slot[g] < 0) {
+                if (p < len) atomicOr(&st->oob, 1u);
+                continue;
+            }
+            const int64_t t = p + other_rs[l[g] + e[g]];
+            const bool keep = (x[g] & kHeadBit) && !(second_side && e[g]);
+            if (in_range(t, len_out, st)) out[t] = ((x[g] & kIndexMask) + kofs) | (keep ? kHeadBit : 0u);
+        }
     }
 }
 
@@ -202,7 +243,9 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
         FSP_CUDA(cudaMemsetAsync(rsB, 0, 4, s));
     }
     if (na + nb > 0) {
-        merge_columns_kernel<<<grid_for(a.n), 256, 0, s>>>(a.jcS, a.irS, b.jcS, b.irS, a.n, lbA, eqA, lbB, eqB);
+        const int cgrid = (int)std::max<int64_t>(
+            1, std::min<int64_t>((a.n + kColThreads - 1) / kColThreads, (int64_t)sm_count(0) * 16));
+        merge_columns_kernel<<<cgrid, kColThreads, 0, s>>>(a.jcS, a.irS, b.jcS, b.irS, a.n, lbA, eqA, lbB, eqB);
         FSP_LAUNCHED();
     }
     if ((e = exclusive_scan_u32(eqA, shA, na, st, scratch, s)) != FSPARSE_OK) return e;
@@ -220,12 +263,12 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
     merged_nnz_kernel<<<1, 1, 0, s>>>(na, nb, shA + na, st);
     FSP_LAUNCHED();
     if (a.len > 0) {
-        merge_positions_kernel<<<grid_for((a.len + 7) / 8), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, na, lbA,
+        merge_positions_kernel<<<grid_for((a.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, na, lbA,
                                                                         eqA, rsB, 0, 0u, out.perm, out.len, st);
         FSP_LAUNCHED();
     }
     if (b.len > 0) {
-        merge_positions_kernel<<<grid_for((b.len + 7) / 8), 256, 0, s>>>(b.perm, b.chunk_slot0, b.len, nb, lbB,
+        merge_positions_kernel<<<grid_for((b.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(b.perm, b.chunk_slot0, b.len, nb, lbB,
                                                                         eqB, rsA, 1, (uint32_t)a.len, out.perm,
                                                                         out.len, st);
         FSP_LAUNCHED();
