@@ -115,6 +115,27 @@ def test_config_resolution_is_host_logic(lib):
     assert fsparse.fsparse_get_config(93148704, 10**6, 10**6) == c
 
 
+@pytest.mark.parametrize("strategy,ok", [(fsparse.SORT_AUTO, True), (fsparse.SORT_ONESWEEP, True),
+                                         (fsparse.SORT_BUCKET, True), (fsparse.SORT_BUCKET_RADIX, True),
+                                         (4, False), (-1, True)])
+def test_strategy_override_range(lib, strategy, ok):
+    """The four strategies are accepted as overrides (a value <= 0 leaves the
+    strategy to the tuner); anything above is an argument error."""
+    cfg = {"strategy": strategy, "radix_bits": 0, "sweep_items": 0, "sweep_threads": 0,
+           "bucket_target": 0, "numeric_tile": 0}
+    try:
+        if ok:
+            fsparse.fsparse_set_config(cfg)
+            c = fsparse.fsparse_get_config(93148704, 10**6, 10**6)
+            if strategy > 0:
+                assert c["strategy"] == strategy
+        else:
+            with pytest.raises(fsparse.FsparseError):
+                fsparse.fsparse_set_config(cfg)
+    finally:
+        fsparse.fsparse_set_config(None)
+
+
 def test_tuning_table_roundtrip(lib, tmp_path):
     fsparse.fsparse_tune_clear()
     key = "L%d_K%d" % ((1000000).bit_length(), (999).bit_length() + (499).bit_length())
