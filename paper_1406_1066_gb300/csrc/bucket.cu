@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         // chunk slot bases of chunks starting here are kept, bucket-local.
         uint16_t *s_cs = reinterpret_cast<uint16_t *>(s_bits);   // row bitmap no longer needed
         const int64_t c_first = (b0 + kChunk - 1) >> kChunkShift;
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < IPT; ++i) {
             const int q = warp * 32 * IPT + i * 32 + lane;
             if (q >= nx) continue;
@@ -736,8 +736,15 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     // the scatter for the current width are queued before the host waits:
     // the GPU does not idle across the read (they are redone if the width
     // has to shrink).
-    static thread_local uint32_t *h_largest = nullptr;
-    if (!h_largest) FSP_CUDA(cudaMallocHost(reinterpret_cast<void **>(&h_largest), sizeof(uint32_t)));
+    struct PinnedWord {   // one per host thread, released when the thread ends
+        uint32_t *p = nullptr;
+        ~PinnedWord() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    static thread_local PinnedWord pinned;
+    if (!pinned.p) FSP_CUDA(cudaMallocHost(reinterpret_cast<void **>(&pinned.p), sizeof(uint32_t)));
+    uint32_t *const h_largest = pinned.p;
     cudaEvent_t got_largest = nullptr;
     FSP_CUDA(cudaEventCreateWithFlags(&got_largest, cudaEventDisableTiming));
     struct EventGuard {
