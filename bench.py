@@ -257,6 +257,31 @@ def append_timing(torch, fsparse, ii_d, jj_d, t, full_ms, reps: int = 5):
                     "+ merge); full_assembly_ms assembles all triplets from scratch"}
 
 
+def adjoint_timing(torch, fsparse, ii_d, jj_d, s_d, t, peak, reps: int = 20):
+    """The adjoint ds[k] = dprS[irank[k]] (the backward of the numeric
+    assembly) on the benchmark's own plan; irank is derived once, before the
+    timed launches, which run back to back between two events."""
+    jcS, irS, pr, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n)
+    nnz = plan.nnz
+    dprS = pr[:nnz].clone()
+    ds = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+    for _ in range(3):
+        fsparse.numeric_adjoint(plan, dprS, ds)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fsparse.numeric_adjoint(plan, dprS, ds)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    plan.close()
+    B = 12 * t.L + 8 * nnz
+    return {"ms": ms, "gtps": t.L / ms / 1e6, "algorithmic_bytes": B,
+            "hbm_frac": B / (ms / 1e3) / 1e9 / peak,
+            "note": "irank read 4L + ds written 8L + dprS read 8nnz per launch; inputs larger than L2"}
+
+
 def batched_vs_plain(torch, fsparse, to_dev, steps: int = 100):
     """256 uneven mesh instances: 100 graph-replayed batched steps vs per-plan launches."""
     b = inputs.batch(256, 1416)
@@ -468,6 +493,7 @@ def gpu_arm(args):
         extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev)
     if rank == 0 and world == 1:
         extra["append"] = append_timing(torch, fsparse, ii_d, jj_d, t, full_ms)
+        extra["adjoint"] = adjoint_timing(torch, fsparse, ii_d, jj_d, vals[0], t, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
