@@ -223,7 +223,8 @@ def reference_arm(args):
             "value": value, "unit": "G triplets/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": sample},
+            "config": {"workload": workload_desc(t), "workload_name": t.name,
+                       "numeric_steps": NUMERIC_STEPS, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "G triplets/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "G triplets/s", "h2d_bytes_per_step": 0,
