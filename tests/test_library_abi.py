@@ -150,6 +150,10 @@ def test_tuning_table_roundtrip(lib, tmp_path):
     fsparse.fsparse_tune_save(str(out))
     saved = json.loads(out.read_text())
     assert saved["entries"] == [entry]
+    radix = dict(entry, strategy=fsparse.SORT_BUCKET_RADIX, bucket_target=8192)
+    src.write_text(json.dumps({"version": 1, "entries": [radix]}))
+    fsparse.fsparse_tune_load(str(src))
+    assert fsparse.fsparse_get_config(1000000, 1000, 500)["strategy"] == fsparse.SORT_BUCKET_RADIX
     bad = tmp_path / "bad.json"
     bad.write_text('{"entries": [{"class": "L1_K1", "strategy": 9}]}')
     with pytest.raises(fsparse.FsparseError):
