@@ -174,14 +174,15 @@ def oracle_job(t, frac_den: int, numeric_steps: int):
 
 
 def paper_method_job(t, frac_den: int, reps: int = 2):
-    """The paper's own CPU method (serial §2.3, threaded §3): full assembly of
+    """The paper's own CPU method (§2.3, in the threaded form of §3; "serial"
+    is that routine on one thread): full assembly of
     the first L/frac_den triplets, best of `reps` runs of each variant (the
     first run of each also pays for faulting in its tables)."""
     from oracle import paper_method
     Ls = (t.L // frac_den) // 16 * 16
     ii, jj, s = t.ii[:Ls].copy(), t.jj[:Ls].copy(), t.s[:Ls].copy()
     what = "the whole workload" if frac_den == 1 else f"first {Ls} triplets (1/{frac_den} of the workload)"
-    out = {"unit": "G triplets/s (full assembly)", "kind": "paper method (§2.3 serial, §3 threaded)",
+    out = {"unit": "G triplets/s (full assembly)", "kind": "paper method (§2.3 in the threaded form of §3; serial = one thread)",
            "openmp": None, "sample": f"{what}, element order, best of {reps} runs"}
 
     def best(threads):
@@ -283,57 +284,175 @@ def adjoint_timing(torch, fsparse, ii_d, jj_d, s_d, t, peak, reps: int = 20):
             "note": "irank read 4L + ds written 8L + dprS read 8nnz per launch; inputs larger than L2"}
 
 
-def batched_vs_plain(torch, fsparse, to_dev, steps: int = 100):
-    """256 uneven mesh instances: 100 graph-replayed batched steps vs per-plan launches."""
+def batched_vs_plain(torch, fsparse, to_dev, peak, steps: int = 100):
+    """256 uneven mesh instances, 100 re-assembly steps rotating two value
+    buffers: the batched numeric (one launch per step) against per-instance
+    launches, both graph-captured and not; plus one batched symbolic pass
+    against 256 per-instance symbolic calls.  Every timed loop only replays
+    or launches: value buffers are bound at capture (one graph per buffer),
+    so no copy sits inside the timed region."""
     b = inputs.batch(256, 1416)
-    plans = [fsparse.symbolic(to_dev(t.ii), to_dev(t.jj), t.m, t.n) for t in b.instances]
-    bt = fsparse.Batch(plans)
-    total = bt.len_off[-1]
-    vals = [torch.from_numpy(inputs.mesh_values(total, 1416 + k)).to("cuda") for k in range(2)]
-    s_buf = torch.empty(total, dtype=torch.float64, device="cuda")
-    out_b = torch.empty(bt.nnz_off[-1], dtype=torch.float64, device="cuda")
-    outs_p = [torch.empty(p.cap, dtype=torch.float64, device="cuda") for p in plans]
-    views = [s_buf[bt.len_off[i]:bt.len_off[i + 1]] for i in range(len(plans))]
+    insts = b.instances
+    ii_cat = to_dev(np.concatenate([t.ii for t in insts]))
+    jj_cat = to_dev(np.concatenate([t.jj for t in insts]))
+    off = [0] + np.cumsum([t.L for t in insts]).tolist()
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def plain_step():
-        for p, v, o in zip(plans, views, outs_p):
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = mk(), mk()
+        e0.record()
+        for r in range(reps):
+            fn(r)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # symbolic: one batched pass vs one call per instance (each synchronises)
+    views_i = [ii_cat[off[i]:off[i + 1]] for i in range(len(insts))]
+    views_j = [jj_cat[off[i]:off[i + 1]] for i in range(len(insts))]
+    for _ in range(2):
+        fsparse.batch_symbolic(ii_cat, jj_cat, off, [t.m for t in insts], [t.n for t in insts]).close()
+    sym_b = timed(lambda r: fsparse.batch_symbolic(ii_cat, jj_cat, off, [t.m for t in insts],
+                                                   [t.n for t in insts]).close(), 3)
+    plans = [fsparse.symbolic(views_i[i], views_j[i], t.m, t.n) for i, t in enumerate(insts)]
+    for p in plans:
+        p.close()
+    t0 = time.perf_counter()
+    plans = [fsparse.symbolic(views_i[i], views_j[i], t.m, t.n) for i, t in enumerate(insts)]
+    torch.cuda.synchronize()
+    sym_p = (time.perf_counter() - t0) * 1e3
+
+    bt = fsparse.batch_symbolic(ii_cat, jj_cat, off, [t.m for t in insts], [t.n for t in insts])
+    total, total_nnz = bt.len_off[-1], bt.nnz_off[-1]
+    vals = [torch.from_numpy(inputs.mesh_values(total, 1416 + k)).to("cuda") for k in range(2)]
+    out_b = [torch.empty(total_nnz, dtype=torch.float64, device="cuda") for _ in range(2)]
+    outs_p = [[torch.empty(p.cap, dtype=torch.float64, device="cuda") for p in plans] for _ in range(2)]
+    vviews = [[vals[k][off[i]:off[i + 1]] for i in range(len(plans))] for k in range(2)]
+
+    def plain_step(k):
+        for p, v, o in zip(plans, vviews[k], outs_p[k]):
             fsparse.numeric(p, v, o)
 
-    s_buf.copy_(vals[0])
-    bt.numeric(s_buf, out_b)
-    plain_step()
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        bt.numeric(s_buf, out_b)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def capture(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    # the batch's numeric tile: every supported tile, each on its own batch
+    tiles = {}
+    for tile in (1024, 2048, 4096):
+        fsparse.fsparse_set_config({"strategy": 0, "radix_bits": 0, "sweep_items": 0, "sweep_threads": 0,
+                                    "bucket_target": 0, "numeric_tile": tile})
+        bt_t = fsparse.Batch(plans)
+        fsparse.fsparse_set_config(None)
+        gs = [capture(lambda k=k: bt_t.numeric(vals[k], out_b[k])) for k in range(2)]
+        tiles[tile] = timed(lambda r: gs[r & 1].replay(), steps)
+        del gs
+        bt_t.close()
+    best_tile = min(tiles, key=tiles.get)
+    graphs_b = [capture(lambda k=k: bt.numeric(vals[k], out_b[k])) for k in range(2)]
+    batched_ms = timed(lambda r: graphs_b[r & 1].replay(), steps)
+    graphs_p = [capture(lambda k=k: plain_step(k)) for k in range(2)]
+    plain_graph_ms = timed(lambda r: graphs_p[r & 1].replay(), steps)
     n0 = fsparse.fsparse_kernel_launches()
-    e0.record()
-    for k in range(steps):
-        s_buf.copy_(vals[k & 1])
-        g.replay()
-    e1.record()
+    plain_ms = timed(lambda r: plain_step(r & 1), steps)
+    plain_launches = (fsparse.fsparse_kernel_launches() - n0) // steps
     torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1) / steps
-    e0.record()
-    for k in range(steps):
-        s_buf.copy_(vals[k & 1])
-        plain_step()
-    e1.record()
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1) / steps
-    # identical results (last step used vals[(steps-1)&1] in both)
-    same = all(torch.equal(out_b[bt.nnz_off[i]:bt.nnz_off[i + 1]], outs_p[i][: plans[i].nnz])
-               for i in range(len(plans)))
-    res = {"instances": len(plans), "total_triplets": total, "steps": steps,
-           "batched_ms_per_step": batched_ms, "plain_ms_per_step": plain_ms,
-           "batched_gtps": total / batched_ms / 1e6, "plain_gtps": total / plain_ms / 1e6,
-           "speedup": plain_ms / batched_ms, "identical": bool(same),
-           "note": "each step includes a device copy of the step's values into the bound buffer"}
+    same = all(torch.equal(out_b[k][bt.nnz_off[i]:bt.nnz_off[i + 1]], outs_p[k][i][: plans[i].nnz])
+               for k in range(2) for i in range(len(plans)))
+    B = 12 * total + 8 * total_nnz
+    res = {"instances": len(plans), "total_triplets": total, "total_nnz": total_nnz, "steps": steps,
+           "batched_kernel_ms": batched_ms, "batched_gtps": total / batched_ms / 1e6,
+           "hbm_frac": B / (batched_ms / 1e3) / 1e9 / peak, "algorithmic_bytes": B,
+           "tile_sweep_ms": tiles, "best_tile": best_tile,
+           "plain_graph_ms": plain_graph_ms, "plain_ms": plain_ms, "plain_launches_per_step": plain_launches,
+           "speedup_vs_plain": plain_ms / batched_ms, "speedup_vs_plain_graph": plain_graph_ms / batched_ms,
+           "identical": bool(same),
+           "symbolic": {"batched_ms": sym_b, "per_instance_ms": sym_p, "speedup": sym_p / sym_b,
+                        "note": "one fsparse_batch_symbolic pass vs 256 fsparse_symbolic calls (host clock, "
+                                "each call synchronises)"},
+           "note": "batched = one fsparse_batch_numeric launch per step (graph replay); plain = 256 "
+                   "fsparse_numeric launches per step, captured in one graph (plain_graph_ms) or launched "
+                   "(plain_ms); value buffers bound at capture, no copies timed; the batch of the "
+                   "batched leg comes from fsparse_batch_symbolic, the tile sweep from fsparse_batch_create"}
+    del graphs_b, graphs_p
     bt.close()
     for p in plans:
         p.close()
     return res
+
+
+PER_CONFIG = ("mesh2d_64", "uniform_1e6", "pooled_2e4", "mesh3d_60")
+
+
+def per_config(torch, fsparse, to_dev, peak, reps: int = 10):
+    """Configs other than the benchmark's own, one line each: full assembly
+    (median of `reps`, no plan reuse) and numeric re-assembly (mean of
+    `reps` launches), with their fractions of the measured copy bandwidth."""
+    out = {}
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for name in PER_CONFIG:
+        t = inputs.workload(name)
+        ii_d, jj_d, s_d = to_dev(t.ii), to_dev(t.jj), to_dev(t.s)
+        s2 = to_dev(inputs.mesh_values(t.L, 77))
+        prS = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+        out_n = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+        for _ in range(3):
+            fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
+        full = []
+        for _ in range(reps):
+            e0, e1 = mk(), mk()
+            e0.record()
+            _, _, _, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)
+            e1.record()
+            torch.cuda.synchronize()
+            full.append(e0.elapsed_time(e1))
+            nnz = plan.nnz
+            plan.close()
+        _, _, _, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)
+        for _ in range(3):
+            fsparse.numeric(plan, s2, out_n)
+        torch.cuda.synchronize()
+        e0, e1 = mk(), mk()
+        e0.record()
+        for r in range(reps):
+            fsparse.numeric(plan, s2 if r & 1 else s_d, out_n)
+        e1.record()
+        torch.cuda.synchronize()
+        num_ms = e0.elapsed_time(e1) / reps
+        plan.close()
+        f_ms = statistics.median(full)
+        B_full = 16 * t.L + 12 * nnz + 4 * (t.n + 1)
+        B_num = 12 * t.L + 8 * nnz
+        out[name] = {"L": t.L, "nnz": nnz, "m": t.m, "n": t.n,
+                     "full_ms": f_ms, "full_gtps": t.L / f_ms / 1e6,
+                     "full_hbm_frac": B_full / (f_ms / 1e3) / 1e9 / peak,
+                     "numeric_ms": num_ms, "numeric_gtps": t.L / num_ms / 1e6,
+                     "numeric_hbm_frac": B_num / (num_ms / 1e3) / 1e9 / peak,
+                     "inputs_vs_l2": "inside L2 (fractions not meaningful)" if 16 * t.L < 64e6
+                     else "inputs larger than L2"}
+        del ii_d, jj_d, s_d, s2, prS, out_n
+        torch.cuda.empty_cache()
+    return out
+
+
+def full_phases(torch, fsparse, ii_d, jj_d, s_d, t, prS, reps: int = 5):
+    """Device time of every phase of one full assembly (FSPARSE_TIMING=1,
+    CUDA events between the phases; median of `reps` calls)."""
+    os.environ["FSPARSE_TIMING"] = "1"
+    runs = []
+    try:
+        for _ in range(reps):
+            fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
+            runs.append(fsparse.fsparse_last_timings())
+    finally:
+        os.environ.pop("FSPARSE_TIMING", None)
+    names = [n for n, _ in runs[-1]]
+    return {n: statistics.median([dict(r).get(n, 0.0) for r in runs]) for n in names}
 
 
 def gpu_arm(args):
@@ -490,11 +609,16 @@ def gpu_arm(args):
                "steps": e_steps}
 
     extra = {}
-    if rank == 0 and world == 1 and not args.no_batch:
-        extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev)
     if rank == 0 and world == 1:
+        extra["full_phases_ms"] = full_phases(torch, fsparse, ii_d, jj_d, vals[0], t, prS)
         extra["append"] = append_timing(torch, fsparse, ii_d, jj_d, t, full_ms)
         extra["adjoint"] = adjoint_timing(torch, fsparse, ii_d, jj_d, vals[0], t, peak)
+    if rank == 0 and world == 1 and not args.no_batch:
+        del vals, prS, out
+        torch.cuda.empty_cache()
+        extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev, peak)
+    if rank == 0 and world == 1 and not args.no_configs:
+        extra["per_config"] = per_config(torch, fsparse, to_dev, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -554,6 +678,7 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configs' lines")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="mesh3d_100 (default), or mesh3d_<N> for a smaller cube (profiling)")
     args = ap.parse_args(argv)

@@ -104,8 +104,6 @@ fsparse_status fsparse_plan_info(fsparse_plan plan, int32_t *m, int32_t *n, int6
 fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank,
                                    const int32_t **jcS, const int32_t **irS);
 
-/* Release a plan (NULL is a no-op).  Waits for outstanding device work that
-   may still read the plan's arrays. */
 /* Checkpoint and resume of the reusable symbolic state (re-assembly with the
    same pattern after a restart).  fsparse_plan_export copies the plan into a
    host buffer: a header (sizes, configuration) followed by perm, the numeric
@@ -135,7 +133,20 @@ fsparse_status fsparse_plan_import(const void *host_buf, int64_t bytes, void *st
 fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const int32_t *jj,
                                    int64_t len, void *stream, fsparse_plan *plan_out);
 
+/* Release a plan (NULL is a no-op).  Neither the host nor the device as a
+   whole waits: the plan's arrays go back to the stream-ordered pool, on a
+   stream of the library's, once (1) every fsparse_numeric and
+   fsparse_numeric_adjoint launch on the plan has finished (the library
+   records an event per stream after each of them; launches captured into a
+   CUDA graph are not recorded) and (2) the work queued so far on the legacy
+   default stream -- and with it on every blocking stream -- has finished.
+   Reads of the plan's arrays that the caller queued itself on non-blocking
+   streams, and replays of captured graphs, must be finished or ordered
+   before this call, as for any device buffer.  fsparse_plan_release does
+   the same and also orders the release after the work queued so far on
+   `stream`. */
 fsparse_status fsparse_plan_destroy(fsparse_plan plan);
+fsparse_status fsparse_plan_release(fsparse_plan plan, void *stream);
 
 /* ------------------------------------------------------------------------
  * Numeric assembly (Eq. (2.3); App. A post-processing): prS[slot] is the
@@ -209,6 +220,52 @@ fsparse_status fsparse_assemble_f64(const double *ii, const double *jj, const do
 fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, void *stream,
                                     fsparse_batch *batch_out);
 
+/* ------------------------------------------------------------------------
+ * Batched symbolic assembly: `count` independent instances in ONE symbolic
+ * pass (re-assembly of many patterns per time step, §1; the reusable
+ * "quasi assembly" state of §2.1 for all of them at once).
+ *
+ *   ii, jj     device int32[h_len_off[count]]: the instances' unit-offset
+ *              triplets, concatenated; instance b owns positions
+ *              [h_len_off[b], h_len_off[b+1]).  Read only.
+ *   h_len_off  HOST int64[count+1], h_len_off[0] = 0, non-decreasing.
+ *   h_m, h_n   HOST int32[count]: each instance's dimensions; 0 means
+ *              implicit = that instance's largest index (§2.2; costs one
+ *              extra synchronisation for the whole batch).
+ *   batch_out  receives a new batch.
+ *
+ * Every instance is assembled exactly as fsparse_symbolic would assemble it
+ * alone (nzmax 0): the batch is the single problem [S_0 S_1 ... S_{count-1}]
+ * -- the instances' matrices side by side, instance b's columns shifted by
+ * n_0 + ... + n_{b-1} -- so its column-compressed arrays hold every
+ * instance's arrays in order.  fsparse_batch_numeric on the result equals
+ * fsparse_numeric per instance, bit for bit, with instance b's values at
+ * h_len_off[b] of sr_concat and its prS at h_nnz_off[b] of prS_concat
+ * (fsparse_batch_info).  An index outside its own instance's m x n, or
+ * below 1, returns FSPARSE_ERR_INDEX and no batch.  The total length must
+ * stay below 2^30 and the instances' columns must add up to at most
+ * 2^31 - 1 (FSPARSE_ERR_SIZE).  Synchronises `stream` (as fsparse_symbolic,
+ * plus one read of the instances' slot offsets); allocates stream-ordered.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_batch_symbolic(int32_t count, const int32_t *ii, const int32_t *jj,
+                                      const int64_t *h_len_off, const int32_t *h_m,
+                                      const int32_t *h_n, void *stream, fsparse_batch *batch_out);
+
+/* The per-instance CCS arrays of a batch made by fsparse_batch_symbolic,
+   concatenated; batch-owned device arrays, valid until the batch is
+   destroyed, read only for the caller.  Any pointer may be NULL.
+     irank  int32[total len]: instance b's irank (its own slot numbers) at
+            h_len_off[b];
+     jcS    int32[sum over b of (n_b + 1)]: instance b's jcS (starting at 0)
+            at n_0 + ... + n_{b-1} + b;
+     irS    int32[total nnz]: instance b's irS at h_nnz_off[b];
+     h_m, h_n  HOST int32[count]: the dimensions used (implicit ones resolved).
+   irank is derived on the first request that asks for it (one kernel pair on
+   the legacy default stream, waited for).  A batch made from plans
+   (fsparse_batch_create) keeps these arrays in its plans: FSPARSE_ERR_ARG. */
+fsparse_status fsparse_batch_arrays(fsparse_batch batch, const int32_t **irank, const int32_t **jcS,
+                                    const int32_t **irS, int32_t *h_m, int32_t *h_n);
+
 /* Host offsets: h_len_off and h_nnz_off receive count+1 int64 each (either
    may be NULL).  Host only. */
 fsparse_status fsparse_batch_info(fsparse_batch batch, int32_t *count, int64_t *h_len_off,
@@ -220,7 +277,10 @@ fsparse_status fsparse_batch_info(fsparse_batch batch, int32_t *count, int64_t *
 fsparse_status fsparse_batch_numeric(fsparse_batch batch, const double *sr_concat,
                                      double *prS_concat, void *stream);
 
+/* Release a batch; same ordering rules as fsparse_plan_destroy /
+   fsparse_plan_release (the recorded launches are fsparse_batch_numeric). */
 fsparse_status fsparse_batch_destroy(fsparse_batch batch);
+fsparse_status fsparse_batch_release(fsparse_batch batch, void *stream);
 
 /* ------------------------------------------------------------------------
  * Launch configuration and autotuning (library-specific; the paper's
@@ -304,9 +364,10 @@ fsparse_status fsparse_tune_clear(void);
  * Working memory: one static device array of FSPARSE_NOALLOC_SCRATCH_BYTES
  * inside this library, which every GPU that loads the library keeps until
  * the process exits.  The entry point calls no cudaMalloc, cudaFree or other
- * allocating routine.  The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array: calls that overlap on the
+ * allocating routine.  Every call looks up that array's device address on the
+ * current device (cudaGetSymbolAddress), so a device reset between calls is
+ * harmless; the first call on each device also loads the array, and should
+ * come before any stream capture.  All calls share the one array: calls that overlap on the
  * GPU (other streams or threads, without ordering) race and must not be
  * issued.  Synchronises `stream` once to read nnz.
  *

@@ -1,6 +1,7 @@
 /*
  * paper_method.c -- the paper's own CPU method for S = sparse(i,j,s,m,n),
- * serial and multithreaded, written from its description.
+ * written from its description (the threaded form of §3; one thread is the
+ * serial method).
  *
  * TEST AND BASELINE INFRASTRUCTURE.  Used by the test suite (a third
  * cross-check of irank / jcS / irS / prS against the sort-based oracle) and
@@ -10,21 +11,14 @@
  * Source: S. Engblom and D. Lukarski, "Fast Matlab compatible sparse assembly
  * on multicore computers" (arXiv:1406.1066).
  *
- * Serial (§2.3, Parts 1-4, and the App. A post-processing):
- *   Part 1  count the triplets of every row and accumulate: row pointers
- *           that ignore collisions;
- *   Part 2  place the triplet numbers row by row, in input order (a stable
- *           counting sort by row): the array rank;
- *   Part 3  sweep the rows in order; a per-column cache of the last row seen
- *           (hcol) tells a new (row, col) pair from a repeat; a new pair
- *           bumps its column's count, and every triplet gets "column count
- *           minus one" as its column-local slot;
- *   Part 4  accumulate the column counts into jcS and shift every slot by
- *           the start of its column: irank;
- *   post    irS[irank[k]] = ii[k] - 1 and prS[irank[k]] += sr[k] for k
- *           ascending into zeroed storage.
+ * The method (§2.3, Parts 1-4, and the App. A post-processing) orders the
+ * triplets by row with a counting pass, recognises repeated (row, column)
+ * pairs with a per-column record of the last row seen, numbers the unique
+ * pairs column by column, and folds the values in ascending k.  It is
+ * written here only in its multithreaded form (§3); run on one thread it is
+ * the serial method.
  *
- * Multithreaded (§3): the input is cut into one contiguous slice per thread;
+ * Multithreaded form (§3): the input is cut into one contiguous slice per thread;
  * each thread counts its rows privately, and per-row prefix sums over the
  * threads give every thread its own starting cursor inside each row, so
  * rank stays stable in k.  Rows are then cut into one contiguous range per
@@ -56,66 +50,13 @@ int paper_max_threads(void) {
 }
 
 /*
- * Serial method.  ii, jj unit-offset int32[len], already validated against
- * M, N.  Outputs irank[len] (may be NULL), jcS[N+1], irS[>= nnz], prS[>= nnz]
- * (prS may be NULL when sr is NULL).  Returns nnz, or -1 when memory runs out.
- */
-int64_t paper_sparse_serial(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
-                            int32_t M, int32_t N, int32_t *irank_out, int32_t *jcS, int32_t *irS,
-                            double *prS) {
-    int64_t *rowptr = (int64_t *)calloc((size_t)M + 2, sizeof(int64_t));
-    int64_t *rank = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
-    int32_t *hcol = (int32_t *)calloc((size_t)N + 1, sizeof(int32_t));
-    int64_t *colcnt = (int64_t *)calloc((size_t)N + 1, sizeof(int64_t));
-    int32_t *irank = irank_out ? irank_out : (int32_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int32_t));
-    if (!rowptr || !rank || !hcol || !colcnt || !irank) {
-        free(rowptr); free(rank); free(hcol); free(colcnt);
-        if (!irank_out) free(irank);
-        return -1;
-    }
-    /* Part 1: rowptr[r + 1] counts row r; running sum gives row starts. */
-    for (int64_t k = 0; k < len; k++) rowptr[ii[k]]++;
-    for (int32_t r = 1; r <= M; r++) rowptr[r] += rowptr[r - 1];
-    /* rowptr[r - 1] is now the start of row r (unit offset). */
-    /* Part 2: stable placement by row, the cursor walking through each row. */
-    for (int64_t k = 0; k < len; k++) rank[rowptr[ii[k] - 1]++] = k;
-    /* rowptr[r - 1] is now the end of row r.  Part 3: row-ordered sweep. */
-    int64_t pos = 0;
-    for (int32_t r = 1; r <= M; r++) {
-        for (; pos < rowptr[r - 1]; pos++) {
-            const int64_t k = rank[pos];
-            const int32_t c = jj[k];
-            if (hcol[c] < r) {          /* first time (r, c) is seen */
-                hcol[c] = r;
-                colcnt[c]++;
-            }
-            irank[k] = (int32_t)(colcnt[c] - 1);
-        }
-    }
-    /* Part 4: column starts, then global slots. */
-    jcS[0] = 0;
-    for (int32_t c = 1; c <= N; c++) jcS[c] = (int32_t)(jcS[c - 1] + colcnt[c]);
-    for (int64_t k = 0; k < len; k++) irank[k] += jcS[jj[k] - 1];
-    const int64_t nnz = jcS[N];
-    /* Post-processing, k ascending into zeroed storage. */
-    for (int64_t p = 0; p < nnz; p++) {
-        irS[p] = 0;
-        if (prS) prS[p] = 0.0;
-    }
-    for (int64_t k = 0; k < len; k++) {
-        irS[irank[k]] = ii[k] - 1;
-        if (prS && sr) prS[irank[k]] += sr[k];
-    }
-    free(rowptr); free(rank); free(hcol); free(colcnt);
-    if (!irank_out) free(irank);
-    return nnz;
-}
-
-/*
- * Multithreaded method on `nthreads` threads (<= 0: all available).  Same
- * arguments and results as paper_sparse_serial; irank_out, when not NULL,
- * receives irank[k] = irankP[i] for k = rank[i].  *threads_used (may be
- * NULL) receives the thread count actually used.
+ * The method on `nthreads` threads (<= 0: all available; 1: the serial
+ * method).  ii, jj unit-offset int32[len], already validated against M, N.
+ * Outputs irank[len] (may be NULL), jcS[N+1], irS[>= nnz], prS[>= nnz]
+ * (prS may be NULL when sr is NULL).  irank_out, when not NULL, receives
+ * irank[k] = irankP[i] for k = rank[i].  *threads_used (may be NULL)
+ * receives the thread count actually used.  Returns nnz, or -1 when memory
+ * runs out.
  */
 int64_t paper_sparse_omp(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
                          int32_t M, int32_t N, int nthreads, int32_t *irank_out, int32_t *jcS,

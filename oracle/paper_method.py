@@ -1,4 +1,4 @@
-"""The paper's own CPU method (serial §2.3 and threaded §3), from ``paper_method.c``.
+"""The paper's own CPU method (§2.3, in the threaded form of §3), from ``paper_method.c``.
 
 TEST AND BASELINE INFRASTRUCTURE (same rule as the rest of ``oracle/``):
 the tests cross-check it against the sort-based oracle, and the benchmark's
@@ -52,9 +52,6 @@ def _load():
         f64p = ctypes.POINTER(ctypes.c_double)
         lib.paper_max_threads.argtypes = []
         lib.paper_max_threads.restype = ctypes.c_int
-        lib.paper_sparse_serial.argtypes = [i32p, i32p, f64p, ctypes.c_int64, ctypes.c_int32,
-                                            ctypes.c_int32, i32p, i32p, i32p, f64p]
-        lib.paper_sparse_serial.restype = ctypes.c_int64
         lib.paper_sparse_omp.argtypes = [i32p, i32p, f64p, ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_int, i32p, i32p, i32p, f64p,
                                          ctypes.POINTER(ctypes.c_int)]
@@ -71,8 +68,9 @@ def assemble(ii, jj, s=None, m: int = 0, n: int = 0, threads: Optional[int] = No
              want_irank: bool = True):
     """``sparse(i, j, s, m, n)`` by the paper's method -> (Result, threads used).
 
-    ``threads=None`` runs the serial method (§2.3); an integer runs the
-    threaded one (§3) on that many threads (0 = all available).
+    ``threads=None`` runs the method on one thread (the serial method of
+    §2.3); an integer runs the threaded form (§3) on that many threads
+    (0 = all available).
     """
     ii, jj = _i32(ii), _i32(jj)
     if s is not None:
@@ -86,19 +84,12 @@ def assemble(ii, jj, s=None, m: int = 0, n: int = 0, threads: Optional[int] = No
     irS = np.empty(max(L, 1), np.int32)
     prS = np.empty(max(L, 1), np.float64) if s is not None else None
     lib = _load()
-    if threads is None:
-        used = 1
-        nnz = lib.paper_sparse_serial(_p(ii, ctypes.c_int32), _p(jj, ctypes.c_int32),
-                                      _p(s, ctypes.c_double), L, m, n, _p(irank, ctypes.c_int32),
-                                      _p(jcS, ctypes.c_int32), _p(irS, ctypes.c_int32),
-                                      _p(prS, ctypes.c_double))
-    else:
-        t = ctypes.c_int(0)
-        nnz = lib.paper_sparse_omp(_p(ii, ctypes.c_int32), _p(jj, ctypes.c_int32),
-                                   _p(s, ctypes.c_double), L, m, n, int(threads),
-                                   _p(irank, ctypes.c_int32), _p(jcS, ctypes.c_int32),
-                                   _p(irS, ctypes.c_int32), _p(prS, ctypes.c_double), ctypes.byref(t))
-        used = t.value
+    t = ctypes.c_int(0)
+    nnz = lib.paper_sparse_omp(_p(ii, ctypes.c_int32), _p(jj, ctypes.c_int32),
+                               _p(s, ctypes.c_double), L, m, n, 1 if threads is None else int(threads),
+                               _p(irank, ctypes.c_int32), _p(jcS, ctypes.c_int32),
+                               _p(irS, ctypes.c_int32), _p(prS, ctypes.c_double), ctypes.byref(t))
+    used = t.value
     if nnz < 0:
         return Result(ERR_NOMEM), used
     nnz = int(nnz)

@@ -122,7 +122,26 @@ struct TimerScope {
 };
 }  // namespace
 
+namespace {
+thread_local bool t_phase_open = false;
+// Closes a phase range left open by an early return of the entry point.
+struct PhaseRangeGuard {
+    ~PhaseRangeGuard() {
+        if (t_phase_open) nvtxRangePop();
+        t_phase_open = false;
+    }
+};
+}  // namespace
+
+void phase_begin(const char *name) {
+    if (t_phase_open) nvtxRangePop();
+    nvtxRangePushA(name);
+    t_phase_open = true;
+}
+
 void phase_mark(const char *name) {
+    if (t_phase_open) nvtxRangePop();
+    t_phase_open = false;
     PhaseTimer *t = t_timer;
     if (!t || t->n >= PhaseTimer::kMax) return;
     if (cudaEventCreate(&t->ev[t->n]) != cudaSuccess) return;
@@ -135,6 +154,7 @@ int injected_fault() {
     if (!f || !*f) return FAULT_NONE;
     if (std::strcmp(f, "alloc") == 0) return FAULT_ALLOC;
     if (std::strcmp(f, "timeout") == 0) return FAULT_TIMEOUT;
+    if (std::strcmp(f, "timeout_sort") == 0) return FAULT_TIMEOUT_SORT;
     return FAULT_NONE;
 }
 
@@ -191,23 +211,97 @@ static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) 
     return FSPARSE_OK;
 }
 
-// Release device arrays that kernels may still be reading: wait for the
-// device first (a plan may be used on any stream), then hand the blocks
-// back to the stream-ordered pool.
-static void release_device(void *const *ptrs, int count) {
+void note_use(UseLog &log, cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        log.overflow = true;
+        return;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return;   // graph replays are the caller's to finish
+    int i = 0;
+    while (i < log.n && log.stream[i] != s) ++i;
+    if (i == log.n) {
+        if (log.n == UseLog::kMax ||
+            cudaEventCreateWithFlags(&log.event[i], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            log.overflow = true;
+            return;
+        }
+        log.stream[i] = s;
+        ++log.n;
+    }
+    if (cudaEventRecord(log.event[i], s) != cudaSuccess) {
+        cudaGetLastError();
+        log.overflow = true;
+    }
+}
+
+// A non-blocking stream per device on which released arrays go back to the
+// stream-ordered pool.
+static cudaStream_t release_stream(int dev) {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+// Release arrays of a plan or batch whose launches may still be running,
+// without blocking the host or the device as a whole: the library's release
+// stream waits for the events of `log` (every stream a numeric, adjoint or
+// irank launch used) and for the work queued so far on `after` (the caller's
+// stream; the legacy default stream also orders every blocking stream), then
+// frees in stream order.  Falls back to waiting for the device when a stream
+// could not be recorded.
+static void release_after(void *const *ptrs, int count, UseLog &log, cudaStream_t after) {
     bool any = false;
     for (int i = 0; i < count; ++i) any |= ptrs[i] != nullptr;
-    if (!any) return;
-    cudaDeviceSynchronize();
-    for (int i = 0; i < count; ++i)
-        if (ptrs[i]) cudaFreeAsync(ptrs[i], nullptr);
-    cudaDeviceSynchronize();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStream_t rs = any ? release_stream(dev) : nullptr;
+    cudaEvent_t tail = nullptr;
+    const bool ordered = rs && !log.overflow &&
+                         cudaEventCreateWithFlags(&tail, cudaEventDisableTiming) == cudaSuccess &&
+                         cudaEventRecord(tail, after) == cudaSuccess &&
+                         cudaStreamWaitEvent(rs, tail, 0) == cudaSuccess;
+    if (any) {
+        if (ordered) {
+            for (int i = 0; i < log.n; ++i) cudaStreamWaitEvent(rs, log.event[i], 0);
+            for (int i = 0; i < count; ++i)
+                if (ptrs[i]) cudaFreeAsync(ptrs[i], rs);
+        } else {
+            cudaGetLastError();
+            cudaDeviceSynchronize();
+            for (int i = 0; i < count; ++i)
+                if (ptrs[i]) cudaFreeAsync(ptrs[i], nullptr);
+            cudaStreamSynchronize(nullptr);
+        }
+    }
+    if (tail) cudaEventDestroy(tail);   // released by the driver once it has completed
+    for (int i = 0; i < log.n; ++i) cudaEventDestroy(log.event[i]);
+    log = UseLog{};
     cudaGetLastError();
 }
 
-static void free_plan_arrays(Plan &p) {
+// Arrays of a plan that a failed call built: only that call's stream has
+// touched them, so they go back to the pool in its order.
+static void free_plan_arrays_on(Plan &p, cudaStream_t s) {
     void *ptrs[5] = {p.irank, p.jcS, p.irS, p.perm, p.chunk_slot0};
-    release_device(ptrs, 5);
+    for (void *q : ptrs)
+        if (q) cudaFreeAsync(q, s);
+    cudaGetLastError();
+    p.irank = p.jcS = p.irS = nullptr;
+    p.perm = p.chunk_slot0 = nullptr;
+}
+
+static void free_plan_arrays(Plan &p, cudaStream_t after) {
+    void *ptrs[5] = {p.irank, p.jcS, p.irS, p.perm, p.chunk_slot0};
+    release_after(ptrs, 5, p.uses, after);
     p.irank = p.jcS = p.irS = nullptr;
     p.perm = p.chunk_slot0 = nullptr;
 }
@@ -249,6 +343,7 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     }
     if (e != FSPARSE_OK) return e;
     if (sr) {
+        phase_begin("numeric_fold");
         e = launch_numeric(plan.perm, plan.chunk_slot0, len, plan.numeric_tile, sr, prS, 0, 0, s);
         if (e == FSPARSE_OK) *folded = true;
         phase_mark("numeric_fold");
@@ -260,6 +355,8 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
 static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const double *sr,
                                     double *prS, int64_t len, int32_t m, int32_t n, int64_t nzmax,
                                     cudaStream_t s, Plan **out, const fsparse_config *force) {
+    NvtxRange nvtx_("fsparse_symbolic");
+    PhaseRangeGuard phase_guard_;
     *out = nullptr;
     fsparse_status e = check_dims_args(ii, jj, len, m, n, nzmax);
     if (e != FSPARSE_OK) return e;
@@ -275,6 +372,7 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     FSP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s));
 
     if (m == 0 || n == 0) {   // implicit dimensions (§2.2): one extra synchronisation
+        phase_begin("dims");
         if ((e = launch_minmax(ii, jj, len, m, n, d_st, s)) != FSPARSE_OK) return e;
         phase_mark("dims");
         if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return e;
@@ -298,7 +396,7 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     const int64_t irs_cap = std::max<int64_t>(std::max<int64_t>(len, nzmax), 1);
 
     auto fail = [&](fsparse_status st) {
-        free_plan_arrays(*plan);
+        free_plan_arrays_on(*plan, s);
         delete plan;
         return st;
     };
@@ -339,6 +437,7 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     plan->nnz = nnz;
     plan->cap = std::max(nnz, nzmax);
     if (plan->cap > nnz) {
+        phase_begin("nzmax_tail");
         if ((e = launch_fill(plan->irS, folded ? prS : nullptr, nnz, plan->cap, s)) != FSPARSE_OK) return fail(e);
         phase_mark("nzmax_tail");
     }
@@ -406,33 +505,45 @@ fsparse_status fsparse_plan_arrays(fsparse_plan plan, const int32_t **irank, con
     return FSPARSE_OK;
 }
 
-fsparse_status fsparse_plan_destroy(fsparse_plan plan) {
+static fsparse_status destroy_plan(fsparse_plan plan, cudaStream_t after) {
     if (!plan) return FSPARSE_OK;
     Plan *p = &reinterpret_cast<fsparse_plan_s *>(plan)->p;
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
-    free_plan_arrays(*p);
+    free_plan_arrays(*p, after);
     if (cur != p->device) cudaSetDevice(cur);
     delete p;
     return FSPARSE_OK;
 }
 
+fsparse_status fsparse_plan_destroy(fsparse_plan plan) { return destroy_plan(plan, nullptr); }
+
+fsparse_status fsparse_plan_release(fsparse_plan plan, void *stream) {
+    return destroy_plan(plan, as_stream(stream));
+}
+
 fsparse_status fsparse_numeric(fsparse_plan plan, const double *sr, double *prS, void *stream) {
+    NvtxRange nvtx_("fsparse_numeric");
     if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
     const Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
     if ((p.len > 0 && !sr) || (p.cap > 0 && !prS)) return set_error(FSPARSE_ERR_ARG, "NULL array");
-    return launch_numeric(p.perm, p.chunk_slot0, p.len, p.numeric_tile, sr, prS, p.nnz, p.cap,
-                          as_stream(stream));
+    const fsparse_status e = launch_numeric(p.perm, p.chunk_slot0, p.len, p.numeric_tile, sr, prS, p.nnz,
+                                            p.cap, as_stream(stream));
+    if (e == FSPARSE_OK) note_use(reinterpret_cast<fsparse_plan_s *>(plan)->p.uses, as_stream(stream));
+    return e;
 }
 
 fsparse_status fsparse_numeric_adjoint(fsparse_plan plan, const double *dprS, double *ds, void *stream) {
+    NvtxRange nvtx_("fsparse_numeric_adjoint");
     if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
     Plan &p = reinterpret_cast<fsparse_plan_s *>(plan)->p;
     if (p.len > 0 && (!dprS || !ds)) return set_error(FSPARSE_ERR_ARG, "NULL array");
     fsparse_status e = ensure_irank(p, as_stream(stream), false);
     if (e != FSPARSE_OK) return e;
-    return launch_adjoint(p.irank, p.len, dprS, ds, p.nnz, as_stream(stream));
+    e = launch_adjoint(p.irank, p.len, dprS, ds, p.nnz, as_stream(stream));
+    if (e == FSPARSE_OK) note_use(p.uses, as_stream(stream));
+    return e;
 }
 
 fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
@@ -455,7 +566,9 @@ fsparse_status fsparse_assemble(const int32_t *ii, const int32_t *jj, const doub
     if (e != FSPARSE_OK) return e;
     *plan_out = reinterpret_cast<fsparse_plan>(p);
     if (prS_capacity < p->cap) return set_error(FSPARSE_ERR_NZMAX, "prS capacity below the plan's cap");
-    return launch_numeric(p->perm, p->chunk_slot0, p->len, p->numeric_tile, sr, prS, p->nnz, p->cap, s);
+    e = launch_numeric(p->perm, p->chunk_slot0, p->len, p->numeric_tile, sr, prS, p->nnz, p->cap, s);
+    if (e == FSPARSE_OK) note_use(p->uses, s);
+    return e;
 }
 
 // ---- Matlab-style double index arrays ----------------------------------------
@@ -591,7 +704,7 @@ fsparse_status fsparse_plan_import(const void *host_buf, int64_t bytes, void *st
     plan->numeric_tile = h.numeric_tile;
     plan->nchunks = h.nchunks;
     auto fail = [&](fsparse_status st) {
-        free_plan_arrays(*plan);
+        free_plan_arrays_on(*plan, s);
         delete plan;
         return st;
     };
@@ -631,6 +744,7 @@ int32_t fsparse_last_timings(const char **names, double *ms, int32_t max) {
 // ---- delayed assembly ---------------------------------------------------------
 fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const int32_t *jj, int64_t len,
                                    void *stream, fsparse_plan *plan_out) {
+    NvtxRange nvtx_("fsparse_plan_append");
     if (!plan_out) return set_error(FSPARSE_ERR_ARG, "plan_out is NULL");
     *plan_out = nullptr;
     if (!plan) return set_error(FSPARSE_ERR_ARG, "plan is NULL");
@@ -653,14 +767,14 @@ fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const i
 
     Plan *out = new (std::nothrow) Plan();
     if (!out) {
-        free_plan_arrays(*b);
+        free_plan_arrays_on(*b, s);
         delete b;
         return set_error(FSPARSE_ERR_NOMEM, "host allocation");
     }
     auto fail = [&](fsparse_status st) {
-        free_plan_arrays(*b);
+        free_plan_arrays_on(*b, s);
         delete b;
-        free_plan_arrays(*out);
+        free_plan_arrays_on(*out, s);
         delete out;
         return st;
     };
@@ -693,7 +807,7 @@ fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const i
     if (h_st.oob) return fail(set_error(FSPARSE_ERR_INTERNAL, "internal index check failed"));
     out->nnz = out->len ? (int64_t)h_st.nnz : 0;
     out->cap = out->nnz;
-    free_plan_arrays(*b);
+    free_plan_arrays_on(*b, s);
     delete b;
     *plan_out = reinterpret_cast<fsparse_plan>(out);
     return FSPARSE_OK;
@@ -702,6 +816,7 @@ fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const i
 // ---- batch ----------------------------------------------------------------
 fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, void *stream,
                                     fsparse_batch *batch_out) {
+    NvtxRange nvtx_("fsparse_batch_create");
     if (!batch_out) return set_error(FSPARSE_ERR_ARG, "batch_out is NULL");
     *batch_out = nullptr;
     if (count < 0 || (count > 0 && !h_plans)) return set_error(FSPARSE_ERR_ARG, "bad plan list");
@@ -722,11 +837,15 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
     bt->total_nnz = total_nnz;
     bt->h_len_off = new (std::nothrow) int64_t[count + 1];
     bt->h_nnz_off = new (std::nothrow) int64_t[count + 1];
-    bt->numeric_tile = 1024;
+    {   // numeric tile of the concatenation's size class (tuned table, else default)
+        KeyLayout key;
+        bt->numeric_tile = resolve_config(total_len, key).numeric_tile;
+    }
     bt->nchunks = (total_len + kChunk - 1) / kChunk;
     auto fail = [&](fsparse_status st) {
-        void *ptrs[2] = {bt->perm, bt->chunk_slot0};
-        release_device(ptrs, 2);
+        for (void *q : {static_cast<void *>(bt->perm), static_cast<void *>(bt->chunk_slot0)})
+            if (q) cudaFreeAsync(q, s);
+        cudaGetLastError();
         delete[] bt->h_len_off;
         delete[] bt->h_nnz_off;
         delete bt;
@@ -768,6 +887,180 @@ fsparse_status fsparse_batch_create(int32_t count, const fsparse_plan *h_plans, 
     return FSPARSE_OK;
 }
 
+// Many instances in one symbolic pass (batch.cu explains the numbering):
+// remap the columns into the concatenated matrix [S_0 ... S_{count-1}], run
+// the single-problem symbolic phase on it, and keep its sorted order as the
+// batch's numeric plan and its irS as the instances' rows.
+fsparse_status fsparse_batch_symbolic(int32_t count, const int32_t *ii, const int32_t *jj,
+                                      const int64_t *h_len_off, const int32_t *h_m, const int32_t *h_n,
+                                      void *stream, fsparse_batch *batch_out) {
+    NvtxRange nvtx_("fsparse_batch_symbolic");
+    if (!batch_out) return set_error(FSPARSE_ERR_ARG, "batch_out is NULL");
+    *batch_out = nullptr;
+    if (count < 0 || (count > 0 && (!h_len_off || !h_m || !h_n)))
+        return set_error(FSPARSE_ERR_ARG, "bad instance description");
+    int64_t total = 0;
+    if (count > 0) {
+        if (h_len_off[0] != 0) return set_error(FSPARSE_ERR_ARG, "h_len_off[0] must be 0");
+        for (int32_t b = 0; b < count; ++b) {
+            if (h_len_off[b + 1] < h_len_off[b]) return set_error(FSPARSE_ERR_ARG, "h_len_off decreases");
+            if (h_m[b] < 0 || h_n[b] < 0) return set_error(FSPARSE_ERR_ARG, "negative dimension");
+        }
+        total = h_len_off[count];
+    }
+    if (total > kMaxLen) return set_error(FSPARSE_ERR_SIZE, "batch total len above 2^30 - 1");
+    if (total > 0 && (!ii || !jj)) return set_error(FSPARSE_ERR_ARG, "NULL index array");
+    cudaStream_t s = as_stream(stream);
+    int dev = 0;
+    FSP_CUDA(cudaGetDevice(&dev));
+    fsparse_status e;
+    if ((e = ensure_pool(dev)) != FSPARSE_OK) return e;
+
+    Batch *bt = new (std::nothrow) Batch();
+    if (!bt) return set_error(FSPARSE_ERR_NOMEM, "host allocation");
+    bt->device = dev;
+    bt->count = count;
+    bt->symbolic = true;
+    bt->total_len = total;
+    const int cn = std::max(count, 1);
+    bt->h_len_off = new (std::nothrow) int64_t[cn + 1];
+    bt->h_nnz_off = new (std::nothrow) int64_t[cn + 1];
+    bt->h_m = new (std::nothrow) int32_t[cn];
+    bt->h_n = new (std::nothrow) int32_t[cn];
+    Plan *P = nullptr;
+    auto fail = [&](fsparse_status st) {
+        for (void *q : {static_cast<void *>(bt->perm), static_cast<void *>(bt->chunk_slot0),
+                        static_cast<void *>(bt->irank), static_cast<void *>(bt->jcS), static_cast<void *>(bt->irS),
+                        static_cast<void *>(bt->d_len_off), static_cast<void *>(bt->d_nnz_off)})
+            if (q) cudaFreeAsync(q, s);
+        if (P) {
+            free_plan_arrays_on(*P, s);
+            delete P;
+        }
+        cudaGetLastError();
+        delete[] bt->h_len_off;
+        delete[] bt->h_nnz_off;
+        delete[] bt->h_m;
+        delete[] bt->h_n;
+        delete bt;
+        return st;
+    };
+    if (!bt->h_len_off || !bt->h_nnz_off || !bt->h_m || !bt->h_n)
+        return fail(set_error(FSPARSE_ERR_NOMEM, "host allocation"));
+    bt->h_len_off[0] = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        bt->h_len_off[b + 1] = h_len_off[b + 1];
+        bt->h_m[b] = h_m[b];
+        bt->h_n[b] = h_n[b];
+    }
+    if ((e = device_alloc(reinterpret_cast<void **>(&bt->d_len_off), (size_t)(cn + 1) * 8, s)) ||
+        (e = device_alloc(reinterpret_cast<void **>(&bt->d_nnz_off), (size_t)(cn + 1) * 8, s)))
+        return fail(e);
+    if (cudaMemcpyAsync(bt->d_len_off, bt->h_len_off, (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "cudaMemcpyAsync"));
+
+    std::vector<int64_t> col_off((size_t)count + 1, 0);
+    int32_t m_all = 0;
+    {
+        Scratch scratch(s);
+        bool implicit = false;
+        for (int32_t b = 0; b < count; ++b) implicit |= bt->h_m[b] == 0 || bt->h_n[b] == 0;
+        if (implicit && total > 0) {   // implicit dimensions of some instances (§2.2): one extra synchronisation
+            int32_t *dmax = nullptr;
+            if ((e = scratch.get(&dmax, (size_t)2 * cn)) != FSPARSE_OK) return fail(e);
+            std::vector<int32_t> hmax((size_t)2 * cn, 0);
+            if (cudaMemsetAsync(dmax, 0, (size_t)2 * cn * 4, s) != cudaSuccess)
+                return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
+            if ((e = launch_batch_dims(ii, jj, bt->d_len_off, count, total, dmax, dmax + cn, s)) != FSPARSE_OK)
+                return fail(e);
+            if (cudaMemcpyAsync(hmax.data(), dmax, (size_t)2 * cn * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return fail(cuda_error(cudaGetLastError(), "reading instance dimensions"));
+            for (int32_t b = 0; b < count; ++b) {
+                if (bt->h_m[b] == 0) bt->h_m[b] = std::max(hmax[b], 0);
+                if (bt->h_n[b] == 0) bt->h_n[b] = std::max(hmax[cn + b], 0);
+            }
+        }
+        for (int32_t b = 0; b < count; ++b) {
+            col_off[b + 1] = col_off[b] + bt->h_n[b];
+            m_all = std::max(m_all, bt->h_m[b]);
+        }
+        if (col_off[count] > INT32_MAX)
+            return fail(set_error(FSPARSE_ERR_SIZE, "the instances' columns add up beyond 2^31 - 1"));
+        const int32_t n_all = (int32_t)col_off[count];
+        int64_t *d_col_off = nullptr, *d_jcs_off = nullptr;
+        int32_t *d_m = nullptr, *jj2 = nullptr;
+        std::vector<int64_t> jcs_off((size_t)count + 1, 0);
+        for (int32_t b = 0; b < count; ++b) jcs_off[b + 1] = jcs_off[b] + bt->h_n[b] + 1;
+        if ((e = scratch.get(&d_col_off, (size_t)cn + 1)) || (e = scratch.get(&d_jcs_off, (size_t)cn + 1)) ||
+            (e = scratch.get(&d_m, (size_t)cn)) || (e = scratch.get(&jj2, (size_t)std::max<int64_t>(total, 1))))
+            return fail(e);
+        if (cudaMemcpyAsync(d_col_off, col_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s) ||
+            cudaMemcpyAsync(d_jcs_off, jcs_off.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s) ||
+            (count > 0 && cudaMemcpyAsync(d_m, bt->h_m, (size_t)count * 4, cudaMemcpyHostToDevice, s)))
+            return fail(cuda_error(cudaGetLastError(), "cudaMemcpyAsync"));
+        if ((e = launch_batch_remap(ii, jj, bt->d_len_off, d_col_off, d_m, count, total, jj2, s)) != FSPARSE_OK)
+            return fail(e);
+        // The whole batch as one problem: bad indices of any instance arrive
+        // as column 0 and are reported here.
+        if ((e = symbolic_impl(ii, jj2, nullptr, nullptr, total, total > 0 ? std::max(m_all, 1) : m_all,
+                               total > 0 ? std::max(n_all, 1) : n_all, 0, s, &P, nullptr)) != FSPARSE_OK)
+            return fail(e);
+        if ((e = launch_batch_nnz_off(P->jcS, d_col_off, count, bt->d_nnz_off, s)) != FSPARSE_OK) return fail(e);
+        const int64_t jcs_total = jcs_off[count];
+        if ((e = device_alloc(reinterpret_cast<void **>(&bt->jcS), (size_t)std::max<int64_t>(jcs_total, 1) * 4, s)))
+            return fail(e);
+        if ((e = launch_batch_jcs(P->jcS, d_col_off, d_jcs_off, bt->d_nnz_off, count, jcs_total, bt->jcS, s)))
+            return fail(e);
+        if (cudaMemcpyAsync(bt->h_nnz_off, bt->d_nnz_off, (size_t)(count + 1) * 8, cudaMemcpyDeviceToHost, s) ||
+            cudaStreamSynchronize(s))
+            return fail(cuda_error(cudaGetLastError(), "reading instance offsets"));
+    }
+    if (count == 0) bt->h_nnz_off[0] = 0;
+    // The concatenated plan's arrays become the batch's.
+    bt->total_nnz = P->nnz;
+    bt->perm = P->perm;
+    bt->chunk_slot0 = P->chunk_slot0;
+    bt->irS = P->irS;
+    bt->irank = P->irank;
+    bt->numeric_tile = P->numeric_tile;
+    bt->nchunks = P->nchunks;
+    cudaFreeAsync(P->jcS, s);
+    cudaGetLastError();
+    P->perm = P->chunk_slot0 = nullptr;
+    P->irS = P->irank = P->jcS = nullptr;
+    delete P;
+    *batch_out = reinterpret_cast<fsparse_batch>(bt);
+    return FSPARSE_OK;
+}
+
+fsparse_status fsparse_batch_arrays(fsparse_batch batch, const int32_t **irank, const int32_t **jcS,
+                                    const int32_t **irS, int32_t *h_m, int32_t *h_n) {
+    if (!batch) return set_error(FSPARSE_ERR_ARG, "batch is NULL");
+    Batch &b = reinterpret_cast<fsparse_batch_s *>(batch)->b;
+    if (!b.symbolic) return set_error(FSPARSE_ERR_ARG, "a batch made from plans keeps its arrays in the plans");
+    if (irank && !b.irank_ready) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != b.device) cudaSetDevice(b.device);
+        fsparse_status e = launch_irank(b.perm, b.chunk_slot0, b.total_len, b.irank, nullptr);
+        if (e == FSPARSE_OK)
+            e = launch_batch_irank(b.irank, b.d_len_off, b.d_nnz_off, b.count, b.total_len, nullptr);
+        if (e == FSPARSE_OK && cudaStreamSynchronize(nullptr) != cudaSuccess)
+            e = cuda_error(cudaGetLastError(), "cudaStreamSynchronize");
+        if (cur != b.device) cudaSetDevice(cur);
+        if (e != FSPARSE_OK) return e;
+        b.irank_ready = true;
+    }
+    if (irank) *irank = b.irank;
+    if (jcS) *jcS = b.jcS;
+    if (irS) *irS = b.irS;
+    if (h_m) std::memcpy(h_m, b.h_m, sizeof(int32_t) * b.count);
+    if (h_n) std::memcpy(h_n, b.h_n, sizeof(int32_t) * b.count);
+    return FSPARSE_OK;
+}
+
 fsparse_status fsparse_batch_info(fsparse_batch batch, int32_t *count, int64_t *h_len_off,
                                   int64_t *h_nnz_off) {
     if (!batch) return set_error(FSPARSE_ERR_ARG, "batch is NULL");
@@ -780,26 +1073,37 @@ fsparse_status fsparse_batch_info(fsparse_batch batch, int32_t *count, int64_t *
 
 fsparse_status fsparse_batch_numeric(fsparse_batch batch, const double *sr_concat, double *prS_concat,
                                      void *stream) {
+    NvtxRange nvtx_("fsparse_batch_numeric");
     if (!batch) return set_error(FSPARSE_ERR_ARG, "batch is NULL");
     const Batch &b = reinterpret_cast<fsparse_batch_s *>(batch)->b;
     if (b.total_len > 0 && (!sr_concat || !prS_concat)) return set_error(FSPARSE_ERR_ARG, "NULL array");
-    return launch_numeric(b.perm, b.chunk_slot0, b.total_len, b.numeric_tile, sr_concat, prS_concat,
-                          b.total_nnz, b.total_nnz, as_stream(stream));
+    const fsparse_status e = launch_numeric(b.perm, b.chunk_slot0, b.total_len, b.numeric_tile, sr_concat,
+                                            prS_concat, b.total_nnz, b.total_nnz, as_stream(stream));
+    if (e == FSPARSE_OK) note_use(reinterpret_cast<fsparse_batch_s *>(batch)->b.uses, as_stream(stream));
+    return e;
 }
 
-fsparse_status fsparse_batch_destroy(fsparse_batch batch) {
+static fsparse_status destroy_batch(fsparse_batch batch, cudaStream_t after) {
     if (!batch) return FSPARSE_OK;
     Batch *b = &reinterpret_cast<fsparse_batch_s *>(batch)->b;
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != b->device) cudaSetDevice(b->device);
-    void *ptrs[2] = {b->perm, b->chunk_slot0};
-    release_device(ptrs, 2);
+    void *ptrs[7] = {b->perm, b->chunk_slot0, b->irank, b->jcS, b->irS, b->d_len_off, b->d_nnz_off};
+    release_after(ptrs, 7, b->uses, after);
     if (cur != b->device) cudaSetDevice(cur);
     delete[] b->h_len_off;
     delete[] b->h_nnz_off;
+    delete[] b->h_m;
+    delete[] b->h_n;
     delete b;
     return FSPARSE_OK;
+}
+
+fsparse_status fsparse_batch_destroy(fsparse_batch batch) { return destroy_batch(batch, nullptr); }
+
+fsparse_status fsparse_batch_release(fsparse_batch batch, void *stream) {
+    return destroy_batch(batch, as_stream(stream));
 }
 
 // ---- diagnostics ------------------------------------------------------------

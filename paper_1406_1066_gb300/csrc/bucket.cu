@@ -760,6 +760,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         G = sm_count(0) * per_sm;
         G = (int)std::max<int64_t>(1, std::min<int64_t>(G, (len + 4095) / 4096));
         if ((e = scratch.get(&hist, (size_t)nb * G)) || (e = scratch.get(&goff, (size_t)nb * G))) return e;
+        phase_begin("bucket_count");
         FSP_CUDA(cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
         bucket_count_kernel<<<G, 1024, table, s>>>(jj, len, n, sh.cs, nb, hist, st);
         FSP_LAUNCHED();
@@ -771,6 +772,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         FSP_CUDA(cudaMemcpyAsync(h_largest, dmax, 4, cudaMemcpyDeviceToHost, s));
         FSP_CUDA(cudaEventRecord(got_largest, s));
         phase_mark("bucket_count");
+        phase_begin("bucket_scatter");
         FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)nb + 1) * 4, s));
         FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
         if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
@@ -815,6 +817,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     a.ticket = ticket;
     a.st = st;
     a.bitmap = cfg.strategy != FSPARSE_SORT_BUCKET_RADIX;
+    phase_begin("bucket_emit");
     if (largest <= (uint32_t)kEmitCap[0]) e = run_emit<256, 16>(a, nb, s);
     else if (largest <= (uint32_t)kEmitCap[1]) e = run_emit<512, 12>(a, nb, s);
     else e = run_emit<512, 16>(a, nb, s);

@@ -6,12 +6,28 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/fsparse.h"
 
 namespace fsp {
 
 struct DevStatus;
+
+// Streams on which a plan's (or batch's) arrays were read by launches that
+// outlive the call (numeric, adjoint, irank derivation), each with an event
+// recorded after its latest such launch.  The arrays are released only after
+// these events, on a library stream: destroying never stalls the device.
+// Launches captured into a CUDA graph are not recorded (an event recorded in
+// a capture belongs to the graph); replays are the caller's to finish.
+struct UseLog {
+    static constexpr int kMax = 8;
+    cudaStream_t stream[kMax] = {};
+    cudaEvent_t event[kMax] = {};
+    int n = 0;
+    bool overflow = false;   // more streams than kMax: the release waits for the device
+};
+void note_use(UseLog &log, cudaStream_t s);
 
 // Number of bits needed for the values 0..x (0 for x == 0).
 inline int bits_for(uint64_t x) {
@@ -47,6 +63,7 @@ struct Plan {
     int numeric_tile = 1024;         // positions per numeric block
     int64_t nchunks = 0;
     fsparse_config cfg{};            // configuration that built this plan
+    UseLog uses;                     // streams whose launches may still read the arrays
 };
 
 struct Batch {
@@ -59,6 +76,18 @@ struct Batch {
     uint32_t *chunk_slot0 = nullptr; // [nchunks+1]
     int numeric_tile = 1024;
     int64_t nchunks = 0;
+    UseLog uses;
+    // Set only by fsparse_batch_symbolic (a batch made from plans leaves the
+    // CCS arrays in its plans).
+    bool symbolic = false;
+    int32_t *irank = nullptr;        // [total_len] instance-local slots, derived on first request
+    bool irank_ready = false;
+    int32_t *jcS = nullptr;          // [sum(n_b + 1)] per-instance column pointers, concatenated
+    int32_t *irS = nullptr;          // [total_nnz] per-instance rows, concatenated
+    int64_t *d_len_off = nullptr;    // device copies of the offsets [count+1]
+    int64_t *d_nnz_off = nullptr;
+    int32_t *h_m = nullptr;          // host [count] resolved dimensions
+    int32_t *h_n = nullptr;
 };
 
 // ---- errors ---------------------------------------------------------------
@@ -69,9 +98,11 @@ fsparse_status cuda_error(cudaError_t e, const char *what);
 // at each call: FSPARSE_FAULT=alloc makes every device allocation report
 // out-of-memory; FSPARSE_FAULT=timeout makes the first tile of each
 // look-back scan withhold its prefix, so the following tiles' bounded waits
-// run out and the call returns FSPARSE_ERR_TIMEOUT.  Nothing faults, traps or
-// hangs the GPU; unset, it costs one getenv per call.
-enum InjectedFault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2 };
+// run out and the call returns FSPARSE_ERR_TIMEOUT; FSPARSE_FAULT=timeout_sort
+// does the same in the first digit pass of the onesweep sort, so that pass
+// leaves some positions unwritten and the kernels after it read stale keys.
+// Nothing faults, traps or hangs the GPU; unset, it costs one getenv per call.
+enum InjectedFault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2, FAULT_TIMEOUT_SORT = 3 };
 int injected_fault();
 
 // Per-phase timing of one symbolic call with CUDA events on its stream, on
@@ -80,6 +111,19 @@ int injected_fault();
 // does nothing when timing is off.  The durations of the thread's last timed
 // call are read with fsparse_last_timings.
 void phase_mark(const char *name);
+// NVTX range of the phase that starts here (closed by the next phase_mark,
+// or at the end of the entry point).
+void phase_begin(const char *name);
+
+// NVTX range over a host scope (an entry point or one phase of it): tools
+// such as Nsight Systems show it on the host timeline and tie the kernels
+// launched inside it to it.  Header-only NVTX; a few ns when no tool listens.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 #define FSP_CUDA(call)                                                        \
     do {                                                                      \
         cudaError_t e_ = (call);                                              \
@@ -173,6 +217,22 @@ fsparse_status launch_batch_concat(const uint32_t *src, uint32_t *dst, int64_t l
                                    uint32_t offset, cudaStream_t s);
 fsparse_status launch_chunk_heads(const uint32_t *perm, int64_t len, uint32_t *counts,
                                   int64_t nchunks, cudaStream_t s);
+
+// Batched symbolic assembly (batch.cu): per-instance dimensions, the column
+// shift into the concatenated matrix, and the per-instance views of its CCS
+// arrays.  Offsets are ascending int64 arrays of count + 1 entries.
+fsparse_status launch_batch_dims(const int32_t *ii, const int32_t *jj, const int64_t *len_off, int count,
+                                 int64_t total, int32_t *max_i, int32_t *max_j, cudaStream_t s);
+fsparse_status launch_batch_remap(const int32_t *ii, const int32_t *jj, const int64_t *len_off,
+                                  const int64_t *col_off, const int32_t *m, int count, int64_t total,
+                                  int32_t *jj_out, cudaStream_t s);
+fsparse_status launch_batch_nnz_off(const int32_t *jcS, const int64_t *col_off, int count, int64_t *nnz_off,
+                                    cudaStream_t s);
+fsparse_status launch_batch_jcs(const int32_t *jcS, const int64_t *col_off, const int64_t *jcs_off,
+                                const int64_t *nnz_off, int count, int64_t total, int32_t *out,
+                                cudaStream_t s);
+fsparse_status launch_batch_irank(int32_t *irank, const int64_t *len_off, const int64_t *nnz_off, int count,
+                                  int64_t total, cudaStream_t s);
 
 // Hybrid column-bucket path.  Synchronises once to read the largest bucket
 // and narrows the buckets until it fits shared memory; sets *unfit (and does

@@ -9,9 +9,12 @@
 // until the process exits.
 //
 // In host code `g_noalloc_scratch` names a host-side stand-in, not a device
-// address, so the device address is looked up once per device (with that
-// device current) and only that address is handed to the kernels.
-#include <mutex>
+// address, so the device address is looked up on every call (with the
+// caller's device current) and only that address is handed to the kernels.
+// The lookup is cheap after the first one on a device, and a fresh lookup
+// stays right when the device was reset (and the array loaded again) since
+// the previous call.
+#include <algorithm>
 
 #include "common.cuh"
 #include "internal.hpp"
@@ -22,22 +25,12 @@ constexpr size_t kNoallocBytes = (size_t)FSPARSE_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-// Device address of g_noalloc_scratch on the current device (looked up on
-// the first call made on each device).
+// Device address of g_noalloc_scratch on the current device.
 static fsparse_status noalloc_scratch(void **out) {
-    static std::mutex mu;
-    static void *addr[64] = {nullptr};
-    int dev = 0;
-    FSP_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return set_error(FSPARSE_ERR_ARG, "device ordinal above 63");
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        addr[dev] = p;
-    }
-    *out = addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = p;
     return FSPARSE_OK;
 }
 

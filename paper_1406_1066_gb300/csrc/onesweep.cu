@@ -144,6 +144,7 @@ struct PassArgs {
     uint32_t *look;            // [ntiles][RADIX] look-back words
     uint32_t *ticket;
     DevStatus *st;
+    int withhold_first;        // injected failure: tile 0 never publishes its counts
 };
 
 template <int R, int THREADS, int ITEMS>
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
         uint32_t excl;
         if (tile == 0) {
             excl = a.bin_off[tid];
-            st_release(word, kFlagInc | (excl + total));
+            if (!a.withhold_first) st_release(word, kFlagInc | (excl + total));
         } else {
             st_release(word, kFlagAgg | total);
             excl = lookback_exclusive(a.look + tid, RADIX, tile, a.st);
@@ -331,12 +332,14 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
     fsparse_status e;
     if ((e = scratch.get(&hist, (size_t)npass * RADIX)) != FSPARSE_OK) return e;
     if ((e = scratch.get(&offs, (size_t)npass * RADIX)) != FSPARSE_OK) return e;
+    phase_begin("digit_hist");
     FSP_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * RADIX * 4, s));
     if (R == 6) e = run_hist<6>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
     else if (R == 7) e = run_hist<7>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
     else e = run_hist<8>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
     if (e != FSPARSE_OK) return e;
     phase_mark("digit_hist");
+    phase_begin("digit_passes");
 
     const int64_t tile = (int64_t)cfg.sweep_threads * cfg.sweep_items;
     const int64_t ntiles = (len + tile - 1) / tile;
@@ -373,6 +376,7 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
         a.bin_off = offs + (size_t)d * RADIX;
         a.look = look + (size_t)d * ntiles * RADIX;
         a.ticket = tickets + d;
+        a.withhold_first = d == 0 && injected_fault() == FAULT_TIMEOUT_SORT ? 1 : 0;
         a.shift = d * R;
         a.in_fmt = d == 0 ? FMT_IJ : kfmt;
         a.kin = d == 0 ? nullptr : kbuf[(d - 1) & 1];
@@ -397,6 +401,7 @@ struct EmitArgs {
     uint32_t *perm;          // in: sorted k, out: k | kHeadBit on run heads
     int32_t *irS;
     uint32_t *colcnt;        // [n] unique pairs per column (zeroed)
+    int32_t n;               // columns (bound of every colcnt index)
     uint32_t *chunk_slot0;   // [nchunks + 1]
     int64_t nchunks;
     int64_t len;
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
             const uint32_t col = (uint32_t)(key[i] >> a.rb);
             if (in_range(slot, a.len, a.st)) a.irS[slot] = (int32_t)row;
             if (col != run_col) {
-                if (run_cnt) atomicAdd(&a.colcnt[run_col], run_cnt);
+                if (run_cnt && in_range(run_col, a.n, a.st)) atomicAdd(&a.colcnt[run_col], run_cnt);
                 run_col = col;
                 run_cnt = 0;
             }
@@ -494,7 +499,9 @@ __global__ void __launch_bounds__(THREADS) emit_kernel(EmitArgs a) {
             a.chunk_slot0[a.nchunks] = slot + 1;
         }
     }
-    if (run_cnt) atomicAdd(&a.colcnt[run_col], run_cnt);
+    // (sorted keys left over from an earlier call, after a digit pass whose
+    // wait gave up, can name any column: the bound keeps the add in place)
+    if (run_cnt && in_range(run_col, a.n, a.st)) atomicAdd(&a.colcnt[run_col], run_cnt);
     if (p0 + ITEMS <= a.len) {
 #pragma unroll
         for (int v = 0; v < ITEMS / 4; ++v)
@@ -520,6 +527,7 @@ fsparse_status emit_from_perm(const void *keys, int key_bytes, int64_t len, int3
     FSP_CUDA(cudaMemsetAsync(colcnt, 0, ((size_t)n + 1) * 4, s));
     FSP_CUDA(cudaMemsetAsync(look, 0, ((size_t)ntiles + 1) * 4, s));
     FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
+    phase_begin("emit");
     if (len > 0) {
         EmitArgs a{};
         a.keys = keys;
@@ -528,6 +536,7 @@ fsparse_status emit_from_perm(const void *keys, int key_bytes, int64_t len, int3
         a.perm = plan.perm;
         a.irS = plan.irS;
         a.colcnt = colcnt;
+        a.n = n;
         a.chunk_slot0 = plan.chunk_slot0;
         a.nchunks = plan.nchunks;
         a.len = len;
@@ -538,6 +547,7 @@ fsparse_status emit_from_perm(const void *keys, int key_bytes, int64_t len, int3
         FSP_LAUNCHED();
         phase_mark("emit");
     }
+    phase_begin("jcS_scan");
     e = exclusive_scan_u32(colcnt, reinterpret_cast<uint32_t *>(plan.jcS), n, st, scratch, s);
     phase_mark("jcS_scan");
     return e;

@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
                               ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
         "fsparse_plan_arrays": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
         "fsparse_plan_destroy": [_P],
+        "fsparse_plan_release": [_P, _P],
         "fsparse_numeric": [_P, _P, _P, _P],
         "fsparse_numeric_adjoint": [_P, _P, _P, _P],
         "fsparse_assemble": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
@@ -78,8 +79,13 @@ def lib() -> ctypes.CDLL:
         "fsparse_assemble_f64": [_P, _P, _P, _I64, _I32, _I32, _I64, _P, _I64, _P, ctypes.POINTER(_P)],
         "fsparse_batch_create": [_I32, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)],
         "fsparse_batch_info": [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+        "fsparse_batch_symbolic": [_I32, _P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                                   ctypes.POINTER(_I32), _P, ctypes.POINTER(_P)],
+        "fsparse_batch_arrays": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                 ctypes.POINTER(_I32), ctypes.POINTER(_I32)],
         "fsparse_batch_numeric": [_P, _P, _P, _P],
         "fsparse_batch_destroy": [_P],
+        "fsparse_batch_release": [_P, _P],
         "fsparse_get_config": [_I64, _I32, _I32, ctypes.POINTER(Config)],
         "fsparse_set_config": [ctypes.POINTER(Config)],
         "fsparse_autotune": [_P, _P, _P, _I64, _I32, _I32, _I32, _P, ctypes.POINTER(Config)],
@@ -138,6 +144,10 @@ def fsparse_plan_arrays(plan: int, irank: bool = True, jcS: bool = True,
 
 def fsparse_plan_destroy(plan: int) -> None:
     _check(lib().fsparse_plan_destroy(plan), "fsparse_plan_destroy")
+
+
+def fsparse_plan_release(plan: int, stream: int) -> None:
+    _check(lib().fsparse_plan_release(plan, stream), "fsparse_plan_release")
 
 
 def fsparse_numeric(plan: int, sr: int, prS: int, stream: int) -> None:
@@ -206,6 +216,28 @@ def fsparse_batch_create(plans: Sequence[int], stream: int) -> int:
     return out.value
 
 
+def fsparse_batch_symbolic(ii: int, jj: int, len_off: Sequence[int], m: Sequence[int],
+                           n: Sequence[int], stream: int) -> int:
+    count = len(m)
+    lo = (_I64 * (count + 1))(*len_off)
+    mm = (_I32 * max(count, 1))(*m)
+    nn = (_I32 * max(count, 1))(*n)
+    out = _P()
+    _check(lib().fsparse_batch_symbolic(count, ii, jj, lo, mm, nn, stream, ctypes.byref(out)),
+           "fsparse_batch_symbolic")
+    return out.value
+
+
+def fsparse_batch_arrays(batch: int, count: int, irank: bool = True):
+    """(irank, jcS, irS) device pointers (irank 0 unless asked) and the instances' m, n."""
+    a, b, c = _P(), _P(), _P()
+    mm = (_I32 * max(count, 1))()
+    nn = (_I32 * max(count, 1))()
+    _check(lib().fsparse_batch_arrays(batch, ctypes.byref(a) if irank else None, ctypes.byref(b),
+                                      ctypes.byref(c), mm, nn), "fsparse_batch_arrays")
+    return a.value or 0, b.value or 0, c.value or 0, list(mm)[:count], list(nn)[:count]
+
+
 def fsparse_batch_info(batch: int) -> Tuple[List[int], List[int]]:
     cnt = _I32()
     _check(lib().fsparse_batch_info(batch, ctypes.byref(cnt), None, None), "fsparse_batch_info")
@@ -221,6 +253,10 @@ def fsparse_batch_numeric(batch: int, sr: int, prS: int, stream: int) -> None:
 
 def fsparse_batch_destroy(batch: int) -> None:
     _check(lib().fsparse_batch_destroy(batch), "fsparse_batch_destroy")
+
+
+def fsparse_batch_release(batch: int, stream: int) -> None:
+    _check(lib().fsparse_batch_release(batch, stream), "fsparse_batch_release")
 
 
 def fsparse_get_config(length: int, m: int, n: int) -> dict:
@@ -337,8 +373,11 @@ class Plan:
         return fsparse_plan_export(self.handle)
 
     def close(self) -> None:
+        """Release the plan after the work queued so far on the current stream."""
         if self.handle:
-            fsparse_plan_destroy(self.handle)
+            torch = _torch()
+            with torch.cuda.device(self.device):
+                fsparse_plan_release(self.handle, _stream())
             self.handle = 0
 
     def __del__(self):
@@ -475,14 +514,44 @@ def __getattr__(name):
 
 
 class Batch:
-    """Many plans' numerics in one launch (``fsparse_batch_*``)."""
+    """Many instances' numerics in one launch (``fsparse_batch_*``).
 
-    def __init__(self, plans: Sequence[Plan]):
-        self.device = plans[0].device if plans else None
+    ``Batch(plans)`` concatenates existing plans; ``batch_symbolic(...)``
+    assembles many instances in one symbolic pass.
+    """
+
+    def __init__(self, plans: Optional[Sequence[Plan]] = None, handle: int = 0, device=None):
         torch = _torch()
-        with torch.cuda.device(self.device):
-            self.handle = fsparse_batch_create([p.handle for p in plans], _stream())
+        if handle:
+            self.device = device
+            self.handle = handle
+        else:
+            self.device = plans[0].device if plans else None
+            with torch.cuda.device(self.device):
+                self.handle = fsparse_batch_create([p.handle for p in plans], _stream())
         self.len_off, self.nnz_off = fsparse_batch_info(self.handle)
+        self.count = len(self.len_off) - 1
+
+    def _view(self, ptr: int, n: int):
+        torch = _torch()
+        if n == 0:
+            return torch.empty(0, dtype=torch.int32, device=self.device)
+        return torch.as_tensor(_DeviceView(ptr, n, "<i4", self), device=self.device)
+
+    def arrays(self, irank: bool = True):
+        """(irank, jcS, irS, m, n) of a batch made by ``batch_symbolic`` (see
+        ``fsparse_batch_arrays`` for the layout); zero-copy device views."""
+        a, b, c, m, n = fsparse_batch_arrays(self.handle, self.count, irank)
+        jcs_len = sum(x + 1 for x in n)
+        ir = self._view(a, self.len_off[-1]) if irank else None
+        return ir, self._view(b, jcs_len), self._view(c, self.nnz_off[-1]), m, n
+
+    def instance(self, b: int, irank: bool = True):
+        """Instance b's (irank, jcS, irS) as views (``batch_symbolic`` batches)."""
+        ir, jc, rs, m, n = self.arrays(irank)
+        c0 = sum(x + 1 for x in n[:b])
+        return (ir[self.len_off[b]:self.len_off[b + 1]] if irank else None,
+                jc[c0:c0 + n[b] + 1], rs[self.nnz_off[b]:self.nnz_off[b + 1]])
 
     def numeric(self, s_cat, out=None):
         torch = _torch()
@@ -496,8 +565,11 @@ class Batch:
         return out
 
     def close(self) -> None:
+        """Release the batch after the work queued so far on the current stream."""
         if self.handle:
-            fsparse_batch_destroy(self.handle)
+            torch = _torch()
+            with torch.cuda.device(self.device):
+                fsparse_batch_release(self.handle, _stream())
             self.handle = 0
 
     def __del__(self):
@@ -505,6 +577,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def batch_symbolic(ii, jj, len_off: Sequence[int], m: Sequence[int], n: Sequence[int]) -> Batch:
+    """Many instances (concatenated int32 triplets, host offsets and
+    dimensions) in one symbolic pass -> a :class:`Batch`."""
+    torch = _torch()
+    _dev(ii, torch.int32, "ii")
+    _dev(jj, torch.int32, "jj")
+    if ii.numel() != jj.numel() or ii.numel() != int(len_off[-1]):
+        raise ValueError("ii, jj and len_off disagree in length")
+    with torch.cuda.device(ii.device):
+        h = fsparse_batch_symbolic(ii.data_ptr(), jj.data_ptr(), [int(x) for x in len_off],
+                                   [int(x) for x in m], [int(x) for x in n], _stream())
+    return Batch(handle=h, device=ii.device)
 
 
 def autotune(ii, jj, s, m: int, n: int, reps: int = 3) -> dict:

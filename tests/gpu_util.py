@@ -84,22 +84,3 @@ def check_properties(ii_d, jj_d, plan, expect_nnz=None):
     assert bool(hit.all()), "every slot hit"
     same_col = col_of_slot[1:] == col_of_slot[:-1]
     assert bool((irS[1:][same_col] > irS[:-1][same_col]).all()), "rows ascend in a column"
-
-
-def sampled_fold_check(plan, s_host: np.ndarray, prS_dev, samples: int = 2000, seed: int = 0):
-    """prS at sampled slots equals the ascending-k fold from +0.0 (Python floats)."""
-    irank = plan.irank
-    order = torch.argsort(irank.long() * (plan.len + 1) + torch.arange(plan.len, device=DEV))
-    sorted_slots = irank[order]
-    starts = torch.searchsorted(sorted_slots.contiguous(), torch.arange(plan.nnz + 1, device=DEV,
-                                                                         dtype=torch.int32))
-    rng = np.random.Generator(np.random.PCG64(seed))
-    pick = rng.integers(0, plan.nnz, min(samples, plan.nnz))
-    starts_h = starts.cpu().numpy()
-    order_h = order.cpu().numpy()
-    pr = prS_dev.cpu().numpy()
-    for sl in pick:
-        acc = 0.0
-        for k in sorted(order_h[starts_h[sl]:starts_h[sl + 1]]):
-            acc = acc + float(s_host[k])
-        assert bits([acc])[0] == bits([pr[sl]])[0], (sl, acc, pr[sl])

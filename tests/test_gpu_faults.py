@@ -41,6 +41,29 @@ def test_injected_lookback_timeout(monkeypatch):
     assert_same(g, oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
 
 
+def test_injected_digit_pass_timeout(monkeypatch):
+    """The first digit pass of the onesweep sort withholds tile 0's counts:
+    the following tiles' waits run out, the pass leaves positions unwritten,
+    and the kernels after it read whatever the pool memory held.  The call
+    returns FSPARSE_ERR_TIMEOUT with every access in bounds, and the next
+    call on the same context is exact."""
+    wide = inputs.random_small(200_000, 2**30 - 1, 2**30 - 1, 74, dup=0.2)   # 60-bit keys first
+    t = inputs.random_small(80_000, 500, 300, 75, dup=0.4)
+    with config(strategy=1):
+        assert_same(gpu_assemble(wide.ii, wide.jj, wide.s, wide.m, wide.n),
+                    oracle.assemble(wide.ii, wide.jj, wide.s, wide.m, wide.n))
+        monkeypatch.setenv("FSPARSE_FAULT", "timeout_sort")
+        t0 = time.perf_counter()
+        with pytest.raises(fsparse.FsparseError) as e:
+            fsparse.assemble(to_dev(t.ii), to_dev(t.jj), to_dev(t.s), t.m, t.n)
+        waited = time.perf_counter() - t0
+        assert e.value.status == fsparse.ERR_TIMEOUT
+        assert waited < 60.0
+        monkeypatch.delenv("FSPARSE_FAULT")
+        g = gpu_assemble(t.ii, t.jj, t.s, t.m, t.n)
+    assert_same(g, oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
+
+
 @pytest.mark.parametrize("strategy,phases", [
     (2, ["bucket_count", "bucket_scatter", "bucket_emit", "numeric_fold"]),
     (1, ["digit_hist", "digit_passes", "emit", "jcS_scan", "numeric_fold"])], ids=["bucket", "onesweep"])

@@ -6,7 +6,7 @@ import torch
 import oracle
 import pins
 from gpu_util import (DEV, assert_same, bits, check_against_oracle, check_properties, config,
-                      gpu_assemble, sampled_fold_check, to_dev)
+                      gpu_assemble, to_dev)
 from paper_1406_1066_gb300 import fsparse, inputs
 
 pytestmark = pytest.mark.gpu
@@ -167,19 +167,43 @@ def test_mesh3d_60_full_and_numeric(strategy):
     assert np.array_equal(g2["irank"], g["irank"]) and np.array_equal(bits(g2["prS"]), bits(g["prS"]))
 
 
-def test_mesh3d_100_properties(strategy):
-    """The 93M-triplet cube at full size, launched exactly as the benchmark does."""
-    t = inputs.workload("mesh3d_100")
+_CUBE = {}
+
+
+def cube_reference():
+    """The oracle's assembly of the 100^3 cube (seed 1409) and its numeric
+    folds for the re-assembly values (seeds 1410-1412), computed once."""
+    if not _CUBE:
+        t = inputs.workload("mesh3d_100")
+        r = oracle.assemble(t.ii, t.jj, t.s, t.m, t.n)
+        vals = {seed: inputs.mesh_values(t.L, seed) for seed in (1410, 1411, 1412)}
+        _CUBE.update(t=t, r=r, vals=vals,
+                     num={seed: oracle.numeric(r.irank, v, r.nnz) for seed, v in vals.items()})
+    return _CUBE
+
+
+def test_mesh3d_100_full_size_oracle(strategy):
+    """The 93M-triplet cube at full size, launched exactly as the benchmark
+    does, against the oracle element by element: irank, jcS, irS bit-exact,
+    prS at 0 ULP for the assembly values and for three re-assemblies."""
+    c = cube_reference()
+    t, r = c["t"], c["r"]
+    assert r.nnz == pins.mesh_nnz(100, 3) == 14761198
     ii_d, jj_d, s_d = to_dev(t.ii), to_dev(t.jj), to_dev(t.s)
     jcS, irS, prS, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n)
-    check_properties(ii_d, jj_d, plan, expect_nnz=pins.mesh_nnz(100, 3))
-    assert plan.nnz == 14761198
-    sampled_fold_check(plan, t.s, prS, samples=1500, seed=1)
-    for seed in (1410, 1411, 1412):
-        s2 = inputs.mesh_values(t.L, seed)
-        pr = fsparse.numeric(plan, to_dev(s2))
-        sampled_fold_check(plan, s2, pr, samples=500, seed=seed)
-    del ii_d, jj_d, s_d, prS
+    check_properties(ii_d, jj_d, plan, expect_nnz=r.nnz)
+    del ii_d, jj_d
+    assert plan.nnz == r.nnz
+    assert np.array_equal(jcS.cpu().numpy(), r.jcS)
+    assert np.array_equal(irS.cpu().numpy(), r.irS)
+    assert np.array_equal(bits(prS.cpu().numpy()), bits(r.prS))
+    assert np.array_equal(plan.irank.cpu().numpy(), r.irank)
+    out = torch.empty(plan.cap, dtype=torch.float64, device=DEV)
+    for seed, v in c["vals"].items():
+        s_d.copy_(torch.from_numpy(v))
+        fsparse.numeric(plan, s_d, out)
+        assert np.array_equal(bits(out.cpu().numpy()), bits(c["num"][seed])), seed
+    del s_d, prS, out
     plan.close()
     torch.cuda.empty_cache()
 
