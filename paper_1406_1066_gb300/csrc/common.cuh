@@ -168,6 +168,21 @@ __device__ __forceinline__ bool in_range(int64_t v, int64_t bound, DevStatus *st
     return false;
 }
 
+// +0.0 + v, exactly, without an FP64 add (FP64 adds are scarce on GB300):
+// equal to v for every v except -0.0, which becomes +0.0 (a NaN stays NaN).
+// Every fold starts a run with it: the App. A insert adds into zeroed storage.
+__device__ __forceinline__ double plus_zero(double v) {
+    const unsigned long long b = __double_as_longlong(v);
+    return __longlong_as_double(b == 0x8000000000000000ull ? 0ull : b);
+}
+
+// Value of triplet x (head bit ignored); an index beyond len, which a valid
+// plan never holds, reads as 0 instead of faulting.
+__device__ __forceinline__ double gather(const double *__restrict__ sr, uint32_t x, int64_t len) {
+    const uint32_t k = x & kIndexMask;
+    return k < len ? __ldg(sr + k) : 0.0;
+}
+
 // Index validation shared by every kernel that reads ii/jj: an index outside
 // [1, dim] is reported and replaced by 1, so nothing downstream can address
 // out of bounds; the host then returns FSPARSE_ERR_INDEX.

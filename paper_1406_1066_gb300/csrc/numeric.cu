@@ -17,20 +17,6 @@
 
 namespace fsp {
 
-// +0.0 + v, exactly, without an FP64 add (FP64 adds are scarce on GB300):
-// equal to v for every v except -0.0, which becomes +0.0 (a NaN stays NaN).
-__device__ __forceinline__ double plus_zero(double v) {
-    const unsigned long long b = __double_as_longlong(v);
-    return __longlong_as_double(b == 0x8000000000000000ull ? 0ull : b);
-}
-
-// Value of triplet x (head bit ignored); an index beyond len, which a valid
-// plan never holds, reads as 0 instead of faulting.
-__device__ __forceinline__ double gather(const double *__restrict__ sr, uint32_t x, int64_t len) {
-    const uint32_t k = x & kIndexMask;
-    return k < len ? __ldg(sr + k) : 0.0;
-}
-
 // Chunked fold.  Positions are cut into chunks of kChunk = 16; the plan keeps,
 // per chunk, the number of runs that start before it (chunk_slot0), so every
 // chunk is processed by one thread with no communication at all:
