@@ -327,18 +327,12 @@ static fsparse_status run_symbolic(const int32_t *ii, const int32_t *jj, const d
     fsparse_status e;
     bool unfit = true;
     const bool bucket = cfg.strategy == FSPARSE_SORT_BUCKET || cfg.strategy == FSPARSE_SORT_BUCKET_RADIX;
-    bool bucket_folded = false;
     if (bucket && bucket_supported(len, plan.n, plan.key, cfg)) {
-        e = bucket_symbolic(ii, jj, sr, prS, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s, &unfit,
-                            &bucket_folded);
+        e = bucket_symbolic(ii, jj, len, plan.m, plan.n, plan.key, cfg, plan, d_st, scratch, s, &unfit);
         if (e != FSPARSE_OK) return e;
     }
     if (!unfit) {
         e = FSPARSE_OK;
-        if (bucket_folded) {   // the values were folded inside the bucket kernel
-            *folded = true;
-            return FSPARSE_OK;
-        }
     } else {
         const void *keys = nullptr;
         int key_bytes = 0;

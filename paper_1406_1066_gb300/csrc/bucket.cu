@@ -29,9 +29,8 @@
 //                perm -- each run in ascending k, since the scatter keeps no
 //                order inside a block: every triplet counts the triplets of
 //                its run with a smaller k and lands that far into the run --,
-//                irS, jcS and the numeric chunk slot bases; in a full
-//                assembly it also folds the values of every run (the
-//                bucket's sorted order stays in shared memory for that).
+//                irS, jcS and the numeric chunk slot bases (the values are
+//                folded by the numeric kernel afterwards).
 //
 // A bucket above the kernel's capacity, or a run longer than kRunSortMax,
 // sets DevStatus::overflow; the host then redoes the call with the global
@@ -187,8 +186,6 @@ struct BucketEmitArgs {
     uint32_t *ticket;
     DevStatus *st;
     int bitmap;   // allow the bitmap counting path (else always the radix passes)
-    const double *sr;   // values to fold inside the kernel (full assembly), or NULL
-    double *prS;        // [>= len] folded values, written when sr is set
 };
 
 template <int THREADS, int IPT>
@@ -210,84 +207,6 @@ struct BucketSmem {
 };
 
 __device__ __forceinline__ int bits_of(uint32_t v) { return v ? 32 - __clz(v) : 0; }
-
-// Fold of one bucket's values inside the emit kernel (full assembly): the
-// bucket's sorted order is in shared memory, s_sorted[q] = k | kHeadBit at
-// run heads for q < nx, and its runs are the slots E, E+1, ... in position
-// order.  Each thread takes kChunk positions; a block scan of the head
-// counts gives every chunk the number of runs that start before it, and
-// the fold itself follows the numeric kernel: every run that starts in the
-// chunk is folded from +0.0 in ascending position order (= ascending k, the
-// order of the App. A insert), the chunk's last run continuing past the
-// chunk until the next head.  Runs never leave their bucket (one column
-// each), so the continuation reads shared memory only.  Needs nx <=
-// THREADS * kChunk; every thread of the block must call it.
-template <int THREADS>
-__device__ __forceinline__ void fold_sorted_bucket(const uint32_t *s_sorted, int nx, uint32_t E,
-                                                   const double *__restrict__ sr, double *__restrict__ prS,
-                                                   int64_t len, uint32_t *s_scan, DevStatus *st) {
-    constexpr int C = kChunk;
-    const int q0 = threadIdx.x * C;
-    const int nval = q0 < nx ? min(C, nx - q0) : 0;
-    uint32_t pm[C];
-    if (nval == C) {
-#pragma unroll
-        for (int v = 0; v < C / 4; ++v) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(s_sorted + q0 + 4 * v);
-            pm[4 * v] = x.x;
-            pm[4 * v + 1] = x.y;
-            pm[4 * v + 2] = x.z;
-            pm[4 * v + 3] = x.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < C; ++i) pm[i] = i < nval ? s_sorted[q0 + i] : 0u;
-    }
-    uint32_t hmask = 0;
-#pragma unroll
-    for (int i = 0; i < C; ++i)
-        if (i < nval && (pm[i] & kHeadBit)) hmask |= 1u << i;
-    uint32_t runs;
-    int64_t slot = (int64_t)E + block_exclusive_scan<THREADS>(__popc(hmask), s_scan, &runs);
-    if (hmask == 0) return;   // inside a run that an earlier chunk folds
-    const int lead = __ffs(hmask) - 1;
-    double v[C];
-#pragma unroll
-    for (int i = 0; i < C; ++i) v[i] = (i >= lead && i < nval) ? gather(sr, pm[i], len) : 0.0;
-    double acc = 0.0;
-    bool open = false;
-#pragma unroll
-    for (int i = 0; i < C; ++i) {
-        if ((hmask >> i) & 1u) {
-            if (open && in_range(slot, len, st)) prS[slot] = acc;
-            slot += open;
-            acc = plus_zero(v[i]);
-            open = true;
-        } else if (open && i < nval) {
-            acc += v[i];
-        }
-    }
-    for (int g = q0 + C; nval == C && g < nx; g += 4) {
-        uint32_t x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = g + u < nx ? s_sorted[g + u] : kHeadBit;
-        int c = 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (c == u && !(x[u] & kHeadBit)) ++c;
-        double w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = u < c ? gather(sr, x[u], len) : 0.0;
-        const int cmax = __reduce_max_sync(__activemask(), c);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (u >= cmax) break;
-            if (u < c) acc += w[u];
-        }
-        if (c < 4) break;
-    }
-    if (in_range(slot, len, st)) prS[slot] = acc;
-}
 
 template <int THREADS, int IPT>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(BucketEmitArgs a) {
@@ -571,7 +490,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             const int64_t gp = b0 + dest;
             const bool head = dest == lo;
             a.perm[gp] = kq | (head ? kHeadBit : 0u);
-            s_slot[q] = (uint16_t)(dest | (head ? 0x8000 : 0));   // for the fold (this q is this thread's)
             if ((gp & (kChunk - 1)) == 0 && in_range((gp >> kChunkShift) - c_first, kMaxBucketCap / kChunk + 1, a.st))
                 s_cs[(gp >> kChunkShift) - c_first] = (uint16_t)(head ? slot : slot + 1);
         }
@@ -579,26 +497,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         const uint32_t E = s_misc[3];
         for (int r = tid; r < (int)U; r += THREADS)
             if (in_range(E + r, a.len, a.st)) a.irS[E + r] = (int32_t)(s_roff[r] + row_lo);
-        if (a.sr) {
-            // The bucket's sorted order into shared memory (in place of the
-            // grouped k: every thread first takes its own entries), then the fold.
-            uint32_t kv[IPT], dv[IPT];
-#pragma unroll
-            for (int i = 0; i < IPT; ++i) {
-                const int q = warp * 32 * IPT + i * 32 + lane;
-                kv[i] = q < nx ? s_k[q] : 0u;
-                dv[i] = q < nx ? s_slot[q] : 0xffffu;
-            }
-            __syncthreads();
-            uint32_t *s_sorted = s_k;
-#pragma unroll
-            for (int i = 0; i < IPT; ++i) {
-                const uint32_t d = dv[i] & 0x1fffu;
-                if (dv[i] != 0xffffu && in_range(d, nx, a.st)) s_sorted[d] = kv[i] | ((dv[i] & 0x8000u) ? kHeadBit : 0u);
-            }
-            __syncthreads();
-            fold_sorted_bucket<THREADS>(s_sorted, nx, E, a.sr, a.prS, a.len, s_scan, a.st);
-        }
         const int64_t c_end = (b0 + nx + kChunk - 1) >> kChunkShift;   // chunks starting in [b0, b0+nx)
         for (int64_t c = c_first + tid; c < c_end; c += THREADS) a.chunk_slot0[c] = E + s_cs[c - c_first];
         // jcS: E + number of unique keys before each column's first key c*R.
@@ -727,7 +625,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
     const uint64_t rmaskx = (1ull << rbits) - 1;
     const uint64_t cmask = (1ull << a.cs) - 1;
     const uint32_t *s_w32 = reinterpret_cast<const uint32_t *>(s_w);   // low words: k and equal key bits
-    uint32_t kv[IPT], dv[IPT];   // sorted entry and its position, for the fused fold
     {
         uint32_t before = wbase;   // heads at earlier positions
         const uint32_t lt = lanemask_lt();
@@ -737,8 +634,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             const bool head = (hb[i] >> lane) & 1u;
             const uint32_t run = before + __popc(hb[i] & lt) - (head ? 0u : 1u);
             before += __popc(hb[i]);
-            dv[i] = 0xffffffffu;
-            kv[i] = 0;
             if (p >= nx) continue;
             const uint32_t slot = E + run;
             const uint64_t v = s_w[p];
@@ -764,8 +659,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             }
             const int64_t gp = b0 + p;
             a.perm[b0 + dest] = k | (dest == lo ? kHeadBit : 0u);
-            kv[i] = k | (dest == lo ? kHeadBit : 0u);
-            dv[i] = (uint32_t)dest;
             if (head) {
                 uint32_t row;
                 if (stash) {
@@ -790,15 +683,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
     }
 
     __syncthreads();
-
-    if (a.sr) {   // fused fold: the sorted order into shared memory (over the sorted words)
-        uint32_t *s_sorted = reinterpret_cast<uint32_t *>(s_w);
-#pragma unroll
-        for (int i = 0; i < IPT; ++i)
-            if (dv[i] != 0xffffffffu && in_range(dv[i], nx, a.st)) s_sorted[dv[i]] = kv[i];
-        __syncthreads();
-        fold_sorted_bucket<THREADS>(s_sorted, nx, E, a.sr, a.prS, a.len, s_scan, a.st);
-    }
 
     // jcS of this bucket's columns: E + exclusive prefix of the unique counts.
     {
@@ -838,12 +722,11 @@ static fsparse_status run_emit(const BucketEmitArgs &a, int64_t nb, cudaStream_t
     return FSPARSE_OK;
 }
 
-fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr, double *prS,
-                               int64_t len, int32_t m, int32_t n, const KeyLayout &key,
+fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                               int32_t n, const KeyLayout &key,
                                const fsparse_config &cfg, Plan &plan, DevStatus *st, Scratch &scratch,
-                               cudaStream_t s, bool *unfit, bool *folded) {
+                               cudaStream_t s, bool *unfit) {
     *unfit = false;
-    *folded = false;
     BucketShape sh;
     if (!bucket_shape(len, n, key, cfg, &sh)) {
         *unfit = true;
@@ -942,14 +825,11 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const doubl
     a.ticket = ticket;
     a.st = st;
     a.bitmap = cfg.strategy != FSPARSE_SORT_BUCKET_RADIX;
-    a.sr = sr;
-    a.prS = prS;
     phase_begin("bucket_emit");
     if (largest <= (uint32_t)kEmitCap[0]) e = run_emit<256, 16>(a, nb, s);
     else if (largest <= (uint32_t)kEmitCap[1]) e = run_emit<512, 12>(a, nb, s);
     else e = run_emit<512, 16>(a, nb, s);
     phase_mark("bucket_emit");
-    if (e == FSPARSE_OK) *folded = sr != nullptr;
     return e;
 }
 

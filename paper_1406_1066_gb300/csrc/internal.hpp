@@ -238,13 +238,11 @@ fsparse_status launch_batch_irank(int32_t *irank, const int64_t *len_off, const 
 // and narrows the buckets until it fits shared memory; sets *unfit (and does
 // nothing else) when no width fits, so the caller takes the onesweep path.
 // A run longer than the in-bucket limit sets DevStatus::overflow instead,
-// and the caller redoes the call with onesweep.  With sr given, the values
-// are folded into prS (capacity >= len) inside the bucket kernel and
-// *folded is set.
-fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, const double *sr, double *prS,
-                               int64_t len, int32_t m, int32_t n, const KeyLayout &key,
-                               const fsparse_config &cfg, Plan &plan, DevStatus *st, Scratch &scratch,
-                               cudaStream_t s, bool *unfit, bool *folded);
+// and the caller redoes the call with onesweep.
+fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len, int32_t m,
+                               int32_t n, const KeyLayout &key, const fsparse_config &cfg,
+                               Plan &plan, DevStatus *st, Scratch &scratch, cudaStream_t s,
+                               bool *unfit);
 bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fsparse_config &cfg);
 
 }  // namespace fsp

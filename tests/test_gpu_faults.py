@@ -65,7 +65,7 @@ def test_injected_digit_pass_timeout(monkeypatch):
 
 
 @pytest.mark.parametrize("strategy,phases", [
-    (2, ["bucket_count", "bucket_scatter", "bucket_emit"]),   # values folded inside the emit
+    (2, ["bucket_count", "bucket_scatter", "bucket_emit", "numeric_fold"]),
     (1, ["digit_hist", "digit_passes", "emit", "jcS_scan", "numeric_fold"])], ids=["bucket", "onesweep"])
 def test_phase_timing(monkeypatch, strategy, phases):
     """FSPARSE_TIMING=1 records the device time of every phase of the call."""
