@@ -146,7 +146,11 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
     __syncthreads();
     const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
     const uint64_t lowmask = (1ull << cs) - 1;
-    constexpr int U = 4;   // index loads of U rounds go out before their atomics
+    // Scalar index loads, consecutive k across the lanes of a warp (so a
+    // warp's words for one bucket land side by side); the loads of U rounds
+    // go out before their atomics.  (16-byte loads of four consecutive k per
+    // thread measured slower: 0.42 against 0.33 ms on the 100^3 cube.)
+    constexpr int U = 4;
     const int64_t B = blockDim.x;
     for (int64_t k0 = c0 + tid; k0 < c1; k0 += U * B) {
         int32_t iv[U], jv[U];
@@ -477,13 +481,18 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                 if (hi - lo > kRunSortMax) {
                     atomicOr(&a.st->overflow, 1u);   // redone by the onesweep path
                 } else {
-                    int rank = 0, r = lo;
-                    for (; r < hi && (r & 3); ++r) rank += s_k[r] < kq;
-                    for (; r + 4 <= hi; r += 4) {
+                    // 16-byte loads from the aligned word at or below lo;
+                    // entries outside [lo, hi) are masked out (they stay
+                    // inside the shared array: hi + 3 <= CAP + 3 words lands
+                    // in the next region at worst).
+                    const uint32_t len = (uint32_t)(hi - lo);
+                    int rank = 0;
+                    for (int r = lo & ~3; r < hi; r += 4) {
                         const uint4 f = *reinterpret_cast<const uint4 *>(s_k + r);
-                        rank += (f.x < kq) + (f.y < kq) + (f.z < kq) + (f.w < kq);
+                        const uint32_t o = (uint32_t)(r - lo);
+                        rank += ((o < len) & (f.x < kq)) + ((o + 1 < len) & (f.y < kq)) +
+                                ((o + 2 < len) & (f.z < kq)) + ((o + 3 < len) & (f.w < kq));
                     }
-                    for (; r < hi; ++r) rank += s_k[r] < kq;
                     dest = lo + rank;
                 }
             }
@@ -645,15 +654,17 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                 if (hi - lo > kRunSortMax) {
                     atomicOr(&a.st->overflow, 1u);   // redone by the onesweep path
                 } else {
-                    // Two words per 16-byte shared load (low words at 0 and 8).
+                    // Two words per 16-byte shared load (low words at 0 and
+                    // 8), from the even position at or below lo; positions
+                    // outside [lo, hi) are masked out.
                     const uint32_t kl = (uint32_t)v;
-                    int rank = 0, q = lo;
-                    if (q & 1) rank += s_w32[2 * q++] < kl;
-                    for (; q + 1 < hi; q += 2) {
+                    const uint32_t len = (uint32_t)(hi - lo);
+                    int rank = 0;
+                    for (int q = lo & ~1; q < hi; q += 2) {
                         const uint4 two = *reinterpret_cast<const uint4 *>(s_w32 + 2 * q);
-                        rank += (two.x < kl) + (two.z < kl);
+                        const uint32_t o = (uint32_t)(q - lo);
+                        rank += ((o < len) & (two.x < kl)) + ((o + 1 < len) & (two.z < kl));
                     }
-                    if (q < hi) rank += s_w32[2 * q] < kl;
                     dest = lo + rank;
                 }
             }
