@@ -283,6 +283,54 @@ fsparse_status fsparse_batch_destroy(fsparse_batch batch);
 fsparse_status fsparse_batch_release(fsparse_batch batch, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Column-sharded assembly on several GPUs (one process per GPU): the
+ * routing steps.  The paper's multicore method (§3) gives every thread a
+ * contiguous range of rows; across GPUs every rank owns a contiguous range
+ * of COLUMNS, h_col_split[r] < j <= h_col_split[r+1] (unit-offset j), so
+ * every slot -- and every column of jcS, irS and prS -- belongs to exactly
+ * one rank, and the output is distributed by column blocks (§2 names a
+ * distributed output as an extension of the method).  The collectives
+ * themselves (an all-to-all of the routed triplets, an exclusive scan of
+ * the ranks' nnz) are the caller's; the Python module
+ * paper_1406_1066_gb300.shard runs them with torch.distributed.
+ *
+ * fsparse_shard_route: rank r's slice of the triplets (device ii, jj int32
+ * [len] unit-offset, sr double[len] or NULL) is partitioned stably by
+ * destination rank: the send arrays (device, [len] each) hold the triplets
+ * for rank 0 first, then rank 1, ..., each group in ascending position of
+ * the slice; send_j holds the column INSIDE the destination's block
+ * (j - h_col_split[dest], unit offset); send_s the values (left alone when
+ * sr is NULL); send_k the slice position of every routed triplet (keep it:
+ * it is the route).  h_counts (host int64[nranks]) receives the group
+ * sizes.  Indices are validated against m, n (> 0): a bad one gives
+ * FSPARSE_ERR_INDEX.  nranks 1..256, h_col_split host int64[nranks+1] from 0
+ * to n, non-decreasing.  Synchronises `stream` once.
+ *
+ * When the slices are taken in rank order and received in source-rank
+ * order, each rank's received triplets are in global triplet order, so its
+ * local fsparse_assemble sums every slot in ascending global k: the result
+ * is the single-GPU assembly, bit for bit, cut into column blocks.
+ *
+ * fsparse_shard_unroute: out[send_k[p]] = back[p] for p < len (device int32
+ * arrays): the values returned for the routed triplets (e.g. their global
+ * slots) land at the slice positions they came from.
+ * fsparse_shard_gather: send_s[p] = sr[send_k[p]]: new values along a kept
+ * route (numeric re-assembly of a sharded pattern).  fsparse_shard_offset:
+ * out[p] = in[p] + add (device int32, in place allowed): a rank's local slot
+ * numbers and column pointers shifted by its slot offset, the exclusive
+ * scan of the ranks' nnz.  All three: no sync, no allocation.
+ * ---------------------------------------------------------------------- */
+fsparse_status fsparse_shard_route(const int32_t *ii, const int32_t *jj, const double *sr, int64_t len,
+                                   int32_t m, int32_t n, int32_t nranks, const int64_t *h_col_split,
+                                   int32_t *send_i, int32_t *send_j, double *send_s, int32_t *send_k,
+                                   int64_t *h_counts, void *stream);
+fsparse_status fsparse_shard_unroute(const int32_t *back, const int32_t *send_k, int64_t len, int32_t *out,
+                                     void *stream);
+fsparse_status fsparse_shard_gather(const double *sr, const int32_t *send_k, int64_t len, double *send_s,
+                                    void *stream);
+fsparse_status fsparse_shard_offset(const int32_t *in, int64_t len, int64_t add, int32_t *out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Launch configuration and autotuning (library-specific; the paper's
  * method has no tuning knobs).
  *

@@ -94,6 +94,11 @@ def lib() -> ctypes.CDLL:
         "fsparse_tune_clear": [],
         "fsparse_assemble_noalloc": [_P, _P, _P, _I64, _I32, _I32, _P, _P, _P, _P,
                                      ctypes.POINTER(_I64), _P],
+        "fsparse_shard_route": [_P, _P, _P, _I64, _I32, _I32, _I32, ctypes.POINTER(_I64), _P, _P, _P, _P,
+                                ctypes.POINTER(_I64), _P],
+        "fsparse_shard_unroute": [_P, _P, _I64, _P, _P],
+        "fsparse_shard_gather": [_P, _P, _I64, _P, _P],
+        "fsparse_shard_offset": [_P, _I64, _I64, _P, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -257,6 +262,30 @@ def fsparse_batch_destroy(batch: int) -> None:
 
 def fsparse_batch_release(batch: int, stream: int) -> None:
     _check(lib().fsparse_batch_release(batch, stream), "fsparse_batch_release")
+
+
+def fsparse_shard_route(ii: int, jj: int, sr: int, length: int, m: int, n: int,
+                        col_split: Sequence[int], send_i: int, send_j: int, send_s: int, send_k: int,
+                        stream: int) -> List[int]:
+    """Route a slice to the owners of its columns; returns the group sizes."""
+    R = len(col_split) - 1
+    split = (_I64 * (R + 1))(*[int(x) for x in col_split])
+    counts = (_I64 * max(R, 1))()
+    _check(lib().fsparse_shard_route(ii, jj, sr, length, m, n, R, split, send_i, send_j, send_s, send_k,
+                                     counts, stream), "fsparse_shard_route")
+    return list(counts)[:R]
+
+
+def fsparse_shard_unroute(back: int, send_k: int, length: int, out: int, stream: int) -> None:
+    _check(lib().fsparse_shard_unroute(back, send_k, length, out, stream), "fsparse_shard_unroute")
+
+
+def fsparse_shard_gather(sr: int, send_k: int, length: int, send_s: int, stream: int) -> None:
+    _check(lib().fsparse_shard_gather(sr, send_k, length, send_s, stream), "fsparse_shard_gather")
+
+
+def fsparse_shard_offset(src: int, length: int, add: int, out: int, stream: int) -> None:
+    _check(lib().fsparse_shard_offset(src, length, add, out, stream), "fsparse_shard_offset")
 
 
 def fsparse_get_config(length: int, m: int, n: int) -> dict:
