@@ -389,7 +389,7 @@ def batched_vs_plain(torch, fsparse, to_dev, peak, steps: int = 100):
 PER_CONFIG = ("mesh2d_64", "uniform_1e6", "pooled_2e4", "mesh3d_60")
 
 
-def per_config(torch, fsparse, to_dev, peak, reps: int = 10):
+def per_config(torch, fsparse, to_dev, peak, reps: int = 10, tune: bool = True):
     """Configs other than the benchmark's own, one line each: full assembly
     (median of `reps`, no plan reuse) and numeric re-assembly (mean of
     `reps` launches), with their fractions of the measured copy bandwidth."""
@@ -401,8 +401,11 @@ def per_config(torch, fsparse, to_dev, peak, reps: int = 10):
         s2 = to_dev(inputs.mesh_values(t.L, 77))
         prS = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
         out_n = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+        if tune:
+            fsparse.autotune(ii_d, jj_d, s_d, t.m, t.n, reps=2)
         for _ in range(3):
             fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
+        phases = full_phases(torch, fsparse, ii_d, jj_d, s_d, t, prS, reps=3)
         full = []
         for _ in range(reps):
             e0, e1 = mk(), mk()
@@ -433,6 +436,7 @@ def per_config(torch, fsparse, to_dev, peak, reps: int = 10):
                      "full_hbm_frac": B_full / (f_ms / 1e3) / 1e9 / peak,
                      "numeric_ms": num_ms, "numeric_gtps": t.L / num_ms / 1e6,
                      "numeric_hbm_frac": B_num / (num_ms / 1e3) / 1e9 / peak,
+                     "full_phases_ms": phases, "launch": fsparse.fsparse_get_config(t.L, t.m, t.n),
                      "inputs_vs_l2": "inside L2 (fractions not meaningful)" if 16 * t.L < 64e6
                      else "inputs larger than L2"}
         del ii_d, jj_d, s_d, s2, prS, out_n
@@ -476,6 +480,16 @@ def gpu_arm(args):
     vals = [to_dev(t.s)] + [to_dev(inputs.mesh_values(L, sd)) for sd in VALUE_SEEDS[1:]]
     prS = torch.empty(L, dtype=torch.float64, device=dev)
     out = torch.empty(L, dtype=torch.float64, device=dev)
+    # The library's autotuner picks the launch configuration for this size
+    # class (sort strategy and shape by symbolic time, then the numeric tile
+    # by repeated folds); it runs before, and outside, the timed region.
+    default_cfg = fsparse.fsparse_get_config(L, t.m, t.n)
+    tune_s = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        fsparse.autotune(ii_d, jj_d, vals[0], t.m, t.n, reps=2)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
     cfg = fsparse.fsparse_get_config(L, t.m, t.n)
 
     def step(timing=None):
@@ -618,7 +632,7 @@ def gpu_arm(args):
         torch.cuda.empty_cache()
         extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev, peak)
     if rank == 0 and world == 1 and not args.no_configs:
-        extra["per_config"] = per_config(torch, fsparse, to_dev, peak)
+        extra["per_config"] = per_config(torch, fsparse, to_dev, peak, tune=not args.no_tune)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -643,7 +657,8 @@ def gpu_arm(args):
                        "nnz": nnz, "l2": "inputs larger than L2 (1.49 GB of triplets per assembly)",
                        "l2_bytes": getattr(props, "L2_cache_size", None), "sm_count": props.multi_processor_count,
                        "device": props.name,
-                       "launch": cfg, "parallelism": f"replicas{world}"},
+                       "launch": cfg, "launch_default": default_cfg, "autotune_s": tune_s,
+                       "parallelism": f"replicas{world}"},
             "full": {"ms": full_ms, "gtps": L / full_ms / 1e6,
                      "algorithmic_bytes": B_full, "hbm_frac": B_full / (full_ms / 1e3) / 1e9 / peak,
                      "hbm_frac_nominal": B_full / (full_ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
@@ -679,6 +694,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other configs' lines")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="mesh3d_100 (default), or mesh3d_<N> for a smaller cube (profiling)")
     args = ap.parse_args(argv)

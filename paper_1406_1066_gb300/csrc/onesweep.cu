@@ -305,9 +305,13 @@ static PassFn pick_pass(int R, int threads, int items) {
 #define FSP_PASS_R(r) \
     FSP_PASS(r, 256, 8) FSP_PASS(r, 256, 12) FSP_PASS(r, 256, 16) \
     FSP_PASS(r, 512, 8) FSP_PASS(r, 512, 12) FSP_PASS(r, 512, 16)
+#define FSP_PASS_R256(r) FSP_PASS(r, 256, 8) FSP_PASS(r, 256, 12) FSP_PASS(r, 256, 16)
     FSP_PASS_R(6)
     FSP_PASS_R(7)
     FSP_PASS_R(8)
+    FSP_PASS_R256(9)
+    FSP_PASS_R256(10)
+#undef FSP_PASS_R256
 #undef FSP_PASS_R
 #undef FSP_PASS
     return nullptr;
@@ -336,7 +340,10 @@ fsparse_status onesweep_sort(const int32_t *ii, const int32_t *jj, int64_t len, 
     FSP_CUDA(cudaMemsetAsync(hist, 0, (size_t)npass * RADIX * 4, s));
     if (R == 6) e = run_hist<6>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
     else if (R == 7) e = run_hist<7>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
-    else e = run_hist<8>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
+    else if (R == 8) e = run_hist<8>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
+    else if (R == 9) e = run_hist<9>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
+    else if (R == 10) e = run_hist<10>(ii, jj, len, m, n, key.rb, npass, hist, offs, st, s);
+    else return set_error(FSPARSE_ERR_ARG, "unsupported digit width");
     if (e != FSPARSE_OK) return e;
     phase_mark("digit_hist");
     phase_begin("digit_passes");

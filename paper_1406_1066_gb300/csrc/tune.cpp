@@ -1,8 +1,11 @@
 // tune.cpp -- launch configuration: built-in defaults, a tuned table keyed by
 // problem size class, a process-wide override, and JSON persistence.
 //
-// Size class = (bits of len, bits of the packed key).  The autotuner itself
-// (timing candidates with CUDA events) is fsparse_autotune in api.cu.
+// Size class = (bits of len, bits of the packed key, bits of len / 2^(column
+// bits)).  The last term is the density -- triplets per column, which sets
+// the bucket width and the run lengths -- as far as it is known before an
+// assembly (nnz is not).  The autotuner itself (timing candidates with CUDA
+// events) is fsparse_autotune in api.cu.
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -21,7 +24,8 @@ static std::map<std::string, fsparse_config> g_table;
 
 static std::string size_class(int64_t len, const KeyLayout &key) {
     char buf[64];
-    std::snprintf(buf, sizeof buf, "L%d_K%d", bits_for((uint64_t)(len > 0 ? len : 0)), key.total());
+    const uint64_t l = (uint64_t)(len > 0 ? len : 0);
+    std::snprintf(buf, sizeof buf, "L%d_K%d_D%d", bits_for(l), key.total(), bits_for(l >> key.cb));
     return buf;
 }
 
@@ -29,8 +33,11 @@ bool config_valid(const fsparse_config &c) {
     const bool items = c.sweep_items == 8 || c.sweep_items == 12 || c.sweep_items == 16;
     const bool threads = c.sweep_threads == 256 || c.sweep_threads == 512;
     const bool tile = c.numeric_tile == 1024 || c.numeric_tile == 2048 || c.numeric_tile == 4096;
-    return c.strategy >= 0 && c.strategy <= 3 && c.radix_bits >= 6 && c.radix_bits <= 8 && items &&
-           threads && c.bucket_target >= 1024 && c.bucket_target <= 16384 && tile;
+    // digits of 9 and 10 bits only in 256-thread passes (their per-warp
+    // counters would not fit shared memory beside a 512-thread tile)
+    const bool radix = c.radix_bits >= 6 && (c.radix_bits <= 8 || (c.radix_bits <= 10 && c.sweep_threads == 256));
+    return c.strategy >= 0 && c.strategy <= 3 && radix && items && threads && c.bucket_target >= 1024 &&
+           c.bucket_target <= 16384 && tile;
 }
 
 fsparse_config default_config(int64_t len, const KeyLayout &key) {
@@ -77,9 +84,12 @@ void tune_store(int64_t len, const KeyLayout &key, const fsparse_config &cfg) {
 std::vector<fsparse_config> tune_candidates(int64_t len, const KeyLayout &key) {
     std::vector<fsparse_config> out;
     const int tile = default_config(len, key).numeric_tile;
-    for (int r = 6; r <= 8; ++r)
+    for (int r = 6; r <= 10; ++r)
         for (int th : {256, 512})
-            for (int it : {8, 12, 16}) out.push_back(fsparse_config{FSPARSE_SORT_ONESWEEP, r, it, th, 8192, tile});
+            for (int it : {8, 12, 16}) {
+                const fsparse_config c{FSPARSE_SORT_ONESWEEP, r, it, th, 8192, tile};
+                if (config_valid(c)) out.push_back(c);
+            }
     for (int strat : {FSPARSE_SORT_BUCKET, FSPARSE_SORT_BUCKET_RADIX})
         for (int bt : {2048, 4096, 8192, 12288}) {
             fsparse_config c{strat, 8, 16, 256, bt, tile};

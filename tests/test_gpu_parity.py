@@ -118,8 +118,9 @@ def test_nonfinite_and_signed_zero(strategy):
     assert bits(g["prS"][2:]).tolist() == bits(r.prS[2:]).tolist() == bits([0.0, 0.0]).tolist()
 
 
-@pytest.mark.parametrize("radix", [6, 7, 8])
-@pytest.mark.parametrize("shape", [(256, 8), (256, 12), (256, 16), (512, 8), (512, 12), (512, 16)])
+@pytest.mark.parametrize("radix,shape", [(r, sh) for r in (6, 7, 8) for sh in
+                                         [(256, 8), (256, 12), (256, 16), (512, 8), (512, 12), (512, 16)]] +
+                         [(r, sh) for r in (9, 10) for sh in [(256, 8), (256, 12), (256, 16)]])
 def test_onesweep_variants(radix, shape):
     t = inputs.mesh3d(11, 21)
     u = inputs.random_small(50000, 3000, 2000, 22, dup=0.4)

@@ -111,6 +111,15 @@ def test_config_resolution_is_host_logic(lib):
     with pytest.raises(fsparse.FsparseError):
         fsparse.fsparse_set_config({"strategy": 1, "radix_bits": 3, "sweep_items": 8,
                                     "sweep_threads": 256, "bucket_target": 8192, "numeric_tile": 4096})
+    # 9- and 10-bit digits only with 256-thread passes
+    for bits, threads, ok in [(9, 256, True), (10, 256, True), (9, 512, False), (11, 256, False)]:
+        cfg = {"strategy": 1, "radix_bits": bits, "sweep_items": 16, "sweep_threads": threads,
+               "bucket_target": 8192, "numeric_tile": 1024}
+        if ok:
+            fsparse.fsparse_set_config(cfg)
+        else:
+            with pytest.raises(fsparse.FsparseError):
+                fsparse.fsparse_set_config(cfg)
     fsparse.fsparse_set_config(None)
     assert fsparse.fsparse_get_config(93148704, 10**6, 10**6) == c
 
@@ -138,7 +147,8 @@ def test_strategy_override_range(lib, strategy, ok):
 
 def test_tuning_table_roundtrip(lib, tmp_path):
     fsparse.fsparse_tune_clear()
-    key = "L%d_K%d" % ((1000000).bit_length(), (999).bit_length() + (499).bit_length())
+    key = "L%d_K%d_D%d" % ((1000000).bit_length(), (999).bit_length() + (499).bit_length(),
+                           (1000000 >> (499).bit_length()).bit_length())
     entry = {"class": key, "strategy": 1, "radix_bits": 6, "sweep_items": 12, "sweep_threads": 512,
              "bucket_target": 4096, "numeric_tile": 1024}
     src = tmp_path / "in.json"
