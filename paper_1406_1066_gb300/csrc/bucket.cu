@@ -101,6 +101,8 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len,
     __syncthreads();
     const int64_t g = blockIdx.x, G = gridDim.x;
     const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
+    // (Counting runs of equal buckets across the lanes first, one add per
+    // run, measured slower here: 0.18 against 0.13 ms on the 100^3 cube.)
     auto count = [&](int32_t j) { atomicAdd(&s_h[(uint32_t)(checked_index(j, n, st) - 1) >> cs], 1u); };
     // scalar head up to a 16-byte boundary, int4 body, scalar tail
     const int64_t v0 = min64(c1, (c0 + 3) & ~int64_t(3)), v1 = max(v0, c1 & ~int64_t(3));
@@ -146,30 +148,51 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
     __syncthreads();
     const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
     const uint64_t lowmask = (1ull << cs) - 1;
-    // Scalar index loads, consecutive k across the lanes of a warp (so a
-    // warp's words for one bucket land side by side); the loads of U rounds
-    // go out before their atomics.  (16-byte loads of four consecutive k per
-    // thread measured slower: 0.42 against 0.33 ms on the 100^3 cube.)
-    constexpr int U = 4;
+    const int lane = tid & 31;
     const int64_t B = blockDim.x;
-    for (int64_t k0 = c0 + tid; k0 < c1; k0 += U * B) {
-        int32_t iv[U], jv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t k = k0 + u * B;
-            iv[u] = k < c1 ? ii[k] : 1;
-            jv[u] = k < c1 ? jj[k] : 1;
+    // One position reservation per run of equal buckets across the lanes of
+    // a warp: the head lane adds the run's length, every lane of the run
+    // takes head's base + its distance to the head (lane order).
+    auto put = [&](int32_t i, int32_t j, int64_t k, bool have) {
+        const uint32_t i0 = have ? (uint32_t)(checked_index(i, m, st) - 1) : 0u;
+        const uint32_t j0 = have ? (uint32_t)(checked_index(j, n, st) - 1) : 0u;
+        const uint32_t b = have ? j0 >> cs : 0xffff0000u | (uint32_t)lane;
+        int head;
+        uint32_t c;
+        lane_runs(b, &head, &c);
+        uint32_t base = 0;
+        if (have && head == lane) base = atomicAdd(&s_cur[b], c);
+        const uint32_t pos = __shfl_sync(0xffffffffu, base, head) + (uint32_t)(lane - head);
+        const uint64_t w = ((uint64_t)(j0 & lowmask) << (rb + kb)) | ((uint64_t)i0 << kb) | (uint64_t)k;
+        if (have && in_range(pos, len, st)) words[pos] = w;
+    };
+    // 16-byte index loads (four consecutive triplets per thread) when both
+    // arrays are 16-byte aligned; scalar head and tail around the aligned body
+    // of the slice.  Loops run warp-uniformly.
+    const int64_t v0 = min64(c1, (c0 + 3) & ~int64_t(3)), v1 = max(v0, c1 & ~int64_t(3));
+    auto scalar = [&](int64_t from, int64_t to) {
+        for (int64_t k0 = from; k0 < to; k0 += B) {
+            const int64_t k = k0 + tid;
+            const bool have = k < to;
+            put(have ? ii[k] : 1, have ? jj[k] : 1, k, have);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t k = k0 + u * B;
-            if (k >= c1) break;
-            const uint32_t i0 = (uint32_t)(checked_index(iv[u], m, st) - 1);
-            const uint32_t j0 = (uint32_t)(checked_index(jv[u], n, st) - 1);
-            const uint32_t pos = atomicAdd(&s_cur[j0 >> cs], 1u);
-            const uint64_t w = ((uint64_t)(j0 & lowmask) << (rb + kb)) | ((uint64_t)i0 << kb) | (uint64_t)k;
-            if (in_range(pos, len, st)) words[pos] = w;
+    };
+    if (((reinterpret_cast<uintptr_t>(ii) | reinterpret_cast<uintptr_t>(jj)) & 15) == 0) {
+        scalar(c0, v0);
+        const int4 *i4 = reinterpret_cast<const int4 *>(ii), *j4 = reinterpret_cast<const int4 *>(jj);
+        for (int64_t q0 = v0 / 4; q0 < v1 / 4; q0 += B) {
+            const int64_t q = q0 + tid;
+            const bool have = q < v1 / 4;
+            const int4 ia = have ? __ldg(i4 + q) : make_int4(1, 1, 1, 1);
+            const int4 ja = have ? __ldg(j4 + q) : make_int4(1, 1, 1, 1);
+            put(ia.x, ja.x, 4 * q, have);
+            put(ia.y, ja.y, 4 * q + 1, have);
+            put(ia.z, ja.z, 4 * q + 2, have);
+            put(ia.w, ja.w, 4 * q + 3, have);
         }
+        scalar(v1, c1);
+    } else {
+        scalar(c0, c1);
     }
 }
 

@@ -127,6 +127,21 @@ __device__ __forceinline__ uint32_t warp_lookback_exclusive(const uint32_t *word
     return excl;
 }
 
+// Runs of equal keys in consecutive lanes of a warp (all 32 lanes call it):
+// *head is the first lane of this lane's run, *count (valid in head lanes)
+// the run's length.  One shared-memory atomic per run instead of one per
+// lane removes the same-address serialisation when neighbouring lanes hold
+// the same key (triplets of one element share columns).  Give lanes without
+// an item a key no real item has, e.g. 0xffff0000 | lane.
+__device__ __forceinline__ void lane_runs(uint32_t key, int *head, uint32_t *count) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const uint32_t hm = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    *head = 31 - __clz(hm & ((2u << lane) - 1u));
+    const uint32_t after = hm & ~((2u << lane) - 1u);   // heads above this lane
+    *count = (after ? (uint32_t)(__ffs(after) - 1) : 32u) - (uint32_t)lane;
+}
+
 // Block-wide exclusive scan of one uint32 per thread; returns the total in
 // *total.  `scratch` needs THREADS/32 + 1 words of shared memory.
 template <int THREADS>

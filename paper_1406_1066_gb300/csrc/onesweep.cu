@@ -216,31 +216,56 @@ __global__ void __launch_bounds__(THREADS) onesweep_pass_kernel(PassArgs a) {
     warp_rank<R, ITEMS>(dig, valid, s_wcnt + warp * RADIX, s_wm + warp * RADIX, rnk);
     __syncthreads();
 
-    // Per digit: exclusive offsets across warps, tile total.
-    uint32_t total = 0;
-    if (tid < RADIX) {
-        for (int w = 0; w < WARPS; ++w) {
-            const uint32_t c = s_wcnt[w * RADIX + tid];
-            s_wcnt[w * RADIX + tid] = total;
-            total += c;
+    // Per digit: exclusive offsets across warps, tile total.  Each thread
+    // owns DPT consecutive digits (more than one when the radix exceeds the
+    // block: 9- and 10-bit digits in 256-thread passes).
+    constexpr int DPT = RADIX > THREADS ? RADIX / THREADS : 1;
+    static_assert(RADIX <= THREADS || RADIX % THREADS == 0, "digits split evenly over the threads");
+    const int d0 = tid * DPT;
+    const bool owner = d0 < RADIX;
+    uint32_t tot[DPT];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < DPT; ++j) {
+        tot[j] = 0;
+        if (owner) {
+            const int d = d0 + j;
+            for (int w = 0; w < WARPS; ++w) {
+                const uint32_t c = s_wcnt[w * RADIX + d];
+                s_wcnt[w * RADIX + d] = tot[j];
+                tot[j] += c;
+            }
+            s_total[d] = tot[j];
+            sum += tot[j];
         }
-        s_total[tid] = total;
     }
     uint32_t tile_sum;
-    const uint32_t local = block_exclusive_scan<THREADS>(tid < RADIX ? total : 0, s_scan, &tile_sum);
-    if (tid < RADIX) {
-        s_local[tid] = local;
-        uint32_t *word = a.look + tile * RADIX + tid;
-        uint32_t excl;
-        if (tile == 0) {
-            excl = a.bin_off[tid];
-            if (!a.withhold_first) st_release(word, kFlagInc | (excl + total));
-        } else {
-            st_release(word, kFlagAgg | total);
-            excl = lookback_exclusive(a.look + tid, RADIX, tile, a.st);
-            st_release(word, kFlagInc | (excl + total));
+    uint32_t local = block_exclusive_scan<THREADS>(owner ? sum : 0, s_scan, &tile_sum);
+    if (owner) {
+        // every aggregate is published before any wait, so the successors'
+        // look-backs never wait on this thread's own waits
+#pragma unroll
+        for (int j = 0; j < DPT; ++j) {
+            const int d = d0 + j;
+            s_local[d] = local;
+            local += tot[j];
+            uint32_t *word = a.look + tile * RADIX + d;
+            if (tile == 0) {
+                s_global[d] = a.bin_off[d];
+                if (!a.withhold_first) st_release(word, kFlagInc | (a.bin_off[d] + tot[j]));
+            } else {
+                st_release(word, kFlagAgg | tot[j]);
+            }
         }
-        s_global[tid] = excl;
+        if (tile > 0) {
+#pragma unroll
+            for (int j = 0; j < DPT; ++j) {
+                const int d = d0 + j;
+                const uint32_t excl = lookback_exclusive(a.look + d, RADIX, tile, a.st);
+                st_release(a.look + tile * RADIX + d, kFlagInc | (excl + tot[j]));
+                s_global[d] = excl;
+            }
+        }
     }
     __syncthreads();
 
