@@ -236,27 +236,29 @@ def reference_arm(args):
 
 # --------------------------------------------------------------------------- GPU arm
 def append_timing(torch, fsparse, ii_d, jj_d, t, full_ms, reps: int = 5):
-    """Delayed assembly: the second half of the workload appended to a plan of
-    the first half, against one full symbolic assembly of everything."""
-    half = t.L // 2
-    base = fsparse.symbolic(ii_d[:half], jj_d[:half], t.m, t.n)
-    ms = []
-    for r in range(reps + 2):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        p2 = fsparse.append(base, ii_d[half:], jj_d[half:])
-        e1.record()
-        torch.cuda.synchronize()
-        if r >= 2:
-            ms.append(e0.elapsed_time(e1))
-        p2.close()
-    base.close()
-    a_ms = statistics.median(ms)
-    return {"ms": a_ms, "appended_triplets": t.L - half, "plan_triplets": half,
-            "gtps_appended": (t.L - half) / a_ms / 1e6, "full_assembly_ms": full_ms,
-            "note": "second half appended to a plan of the first half (symbolic of the new half "
-                    "+ merge); full_assembly_ms assembles all triplets from scratch"}
+    """Delayed assembly: the last part of the workload (half, and 1%) appended
+    to a plan of the rest, against one full assembly of everything."""
+    out = {"full_assembly_ms": full_ms,
+           "note": "the last part appended to a plan of the rest (symbolic of the new part + merge); "
+                   "full_assembly_ms assembles all triplets from scratch"}
+    for name, cut in (("half", t.L // 2), ("one_percent", t.L - t.L // 100)):
+        base = fsparse.symbolic(ii_d[:cut], jj_d[:cut], t.m, t.n)
+        ms = []
+        for r in range(reps + 2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            p2 = fsparse.append(base, ii_d[cut:], jj_d[cut:])
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                ms.append(e0.elapsed_time(e1))
+            p2.close()
+        base.close()
+        a_ms = statistics.median(ms)
+        out[name] = {"ms": a_ms, "appended_triplets": t.L - cut, "plan_triplets": cut,
+                     "gtps_appended": (t.L - cut) / a_ms / 1e6, "vs_full_assembly": full_ms / a_ms}
+    return out
 
 
 def adjoint_timing(torch, fsparse, ii_d, jj_d, s_d, t, peak, reps: int = 20):

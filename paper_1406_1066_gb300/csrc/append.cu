@@ -17,7 +17,8 @@
 //   * positions: an old run moves right by the number of new triplets with a
 //     smaller key; a new run moves right by the number of old triplets with a
 //     key not above its own, so inside a shared slot the old triplets (smaller
-//     k) come first and the run stays in ascending k;
+//     k) come first and the run stays in ascending k; the shift is computed
+//     once per run, then applied to every position of it;
 //   * jcS of the merge: old + new column starts minus the shared keys in
 //     earlier columns.
 #include <algorithm>
@@ -136,23 +137,36 @@ __global__ void merge_jcs_kernel(const int32_t *__restrict__ jc1, const int32_t 
         out[c] = (int32_t)((int64_t)jc1[c] + jc2[c] - shared1[jc1[c]]);
 }
 
+// Shift of every run of one side in the merged order, one thread per slot
+// (lb is non-decreasing along the slots, so the lookups into the other
+// side's run starts are nearly sequential).  For the old side (second_side
+// = 0) a run moves by other_rs[lb]: the new triplets with a smaller key.
+// For the new side it moves by other_rs[lb + eq]: the old triplets with a
+// key not above its own, so inside a shared slot the old triplets come
+// first.  Bit 31 marks a new run whose key the old side also holds: its
+// head bit is dropped (the old run starts that slot).
+__global__ void merge_shift_kernel(int64_t nnz, const uint32_t *__restrict__ lb, const uint32_t *__restrict__ eq,
+                                   const uint32_t *__restrict__ other_rs, int second_side,
+                                   uint32_t *__restrict__ shift) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nnz;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = second_side ? eq[x] : 0u;
+        shift[x] = other_rs[lb[x] + e] | (e ? kHeadBit : 0u);
+    }
+}
+
 // Positions of one side's runs in the merged order, one thread per position
 // (a warp takes 32 consecutive positions, two chunks, so loads and stores
 // are coalesced and the lanes of one run share their lookups).  The slot of
 // a position is the run before the warp's first chunk plus the heads up to
-// it.  For the old side (second_side = 0) a run moves by other_rs[lb]: the
-// new triplets with a smaller key.  For the new side it moves by
-// other_rs[lb + eq]: the old triplets with a key not above its own; its head
-// bit is dropped when the old side holds the same key (the old run starts
-// that slot).  Each warp step handles kGroups such 32-position groups, whose
-// chains of dependent lookups (perm -> slot -> lb/eq -> other_rs) overlap.
+// it; the position moves by its slot's shift.  Each warp step handles
+// kGroups such 32-position groups, whose dependent lookups (perm -> slot ->
+// shift) overlap.
 constexpr int kGroups = 4;
 
 __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ chunk_slot0,
-                                       int64_t len, int64_t nnz, const uint32_t *__restrict__ lb,
-                                       const uint32_t *__restrict__ eq, const uint32_t *__restrict__ other_rs,
-                                       int second_side, uint32_t kofs, uint32_t *__restrict__ out,
-                                       int64_t len_out, DevStatus *st) {
+                                       int64_t len, int64_t nnz, const uint32_t *__restrict__ shift,
+                                       uint32_t kofs, uint32_t *__restrict__ out, int64_t len_out, DevStatus *st) {
     const int lane = threadIdx.x & 31;
     const uint32_t le = lanemask_lt() | (1u << lane);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -166,26 +180,24 @@ __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const 
             x[g] = p < len ? __ldg(perm + p) : 0u;
             base[g] = w0 + 32 * g < len ? __ldg(chunk_slot0 + ((w0 + 32 * g) >> kChunkShift)) : 0u;
         }
-        int64_t slot[kGroups];
-        uint32_t e[kGroups], l[kGroups];
+        uint32_t sh[kGroups];
+        bool ok[kGroups];
 #pragma unroll
         for (int g = 0; g < kGroups; ++g) {
             const uint32_t hm = __ballot_sync(0xffffffffu, (x[g] & kHeadBit) != 0);
-            slot[g] = (int64_t)base[g] - 1 + __popc(hm & le);
-            const bool ok = w0 + 32 * g + lane < len && slot[g] >= 0 && slot[g] < nnz;
-            e[g] = ok && second_side ? __ldg(eq + slot[g]) : 0u;
-            l[g] = ok ? __ldg(lb + slot[g]) : 0u;
-            if (!ok) slot[g] = -1;
+            const int64_t slot = (int64_t)base[g] - 1 + __popc(hm & le);
+            ok[g] = w0 + 32 * g + lane < len && slot >= 0 && slot < nnz;
+            sh[g] = ok[g] ? __ldg(shift + slot) : 0u;
         }
 #pragma unroll
         for (int g = 0; g < kGroups; ++g) {
             const int64_t p = w0 + 32 * g + lane;
-            if (slot[g] < 0) {
+            if (!ok[g]) {
                 if (p < len) atomicOr(&st->oob, 1u);
                 continue;
             }
-            const int64_t t = p + other_rs[l[g] + e[g]];
-            const bool keep = (x[g] & kHeadBit) && !(second_side && e[g]);
+            const int64_t t = p + (sh[g] & kIndexMask);
+            const bool keep = (x[g] & kHeadBit) && !(sh[g] & kHeadBit);
             if (in_range(t, len_out, st)) out[t] = ((x[g] & kIndexMask) + kofs) | (keep ? kHeadBit : 0u);
         }
     }
@@ -224,10 +236,12 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
     const int64_t na = a.nnz, nb = b.nnz;
     uint32_t *rsA, *rsB, *lbA, *eqA, *lbB, *eqB, *shA, *shB;
     fsparse_status e;
+    uint32_t *mvA, *mvB;
     if ((e = scratch.get(&rsA, (size_t)na + 1)) || (e = scratch.get(&rsB, (size_t)nb + 1)) ||
         (e = scratch.get(&lbA, (size_t)na + 1)) || (e = scratch.get(&eqA, (size_t)na + 1)) ||
         (e = scratch.get(&lbB, (size_t)nb + 1)) || (e = scratch.get(&eqB, (size_t)nb + 1)) ||
-        (e = scratch.get(&shA, (size_t)na + 1)) || (e = scratch.get(&shB, (size_t)nb + 1)))
+        (e = scratch.get(&shA, (size_t)na + 1)) || (e = scratch.get(&shB, (size_t)nb + 1)) ||
+        (e = scratch.get(&mvA, (size_t)na + 1)) || (e = scratch.get(&mvB, (size_t)nb + 1)))
         return e;
     // run starts (an empty side has rs = {0})
     if (a.len > 0) {
@@ -262,15 +276,22 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
     FSP_LAUNCHED();
     merged_nnz_kernel<<<1, 1, 0, s>>>(na, nb, shA + na, st);
     FSP_LAUNCHED();
+    if (na > 0) {
+        merge_shift_kernel<<<grid_for(na), 256, 0, s>>>(na, lbA, eqA, rsB, 0, mvA);
+        FSP_LAUNCHED();
+    }
+    if (nb > 0) {
+        merge_shift_kernel<<<grid_for(nb), 256, 0, s>>>(nb, lbB, eqB, rsA, 1, mvB);
+        FSP_LAUNCHED();
+    }
     if (a.len > 0) {
-        merge_positions_kernel<<<grid_for((a.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, na, lbA,
-                                                                        eqA, rsB, 0, 0u, out.perm, out.len, st);
+        merge_positions_kernel<<<grid_for((a.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(
+            a.perm, a.chunk_slot0, a.len, na, mvA, 0u, out.perm, out.len, st);
         FSP_LAUNCHED();
     }
     if (b.len > 0) {
-        merge_positions_kernel<<<grid_for((b.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(b.perm, b.chunk_slot0, b.len, nb, lbB,
-                                                                        eqB, rsA, 1, (uint32_t)a.len, out.perm,
-                                                                        out.len, st);
+        merge_positions_kernel<<<grid_for((b.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(
+            b.perm, b.chunk_slot0, b.len, nb, mvB, (uint32_t)a.len, out.perm, out.len, st);
         FSP_LAUNCHED();
     }
     // chunk slot bases of the merged order; nnz = na + nb - shared
