@@ -556,7 +556,7 @@ def gpu_arm(args):
     B_num = 12 * L + 8 * nnz
     B_full = 16 * L + 12 * nnz + 4 * (t.n + 1)
     achieved = B_num / (num_avg / 1e3) / 1e9
-    src_hash = kernel_source_hash("numeric.cu")
+    src_hash = kernel_source_hash("numeric.cu", "common.cuh")
     traffic = profiled_traffic(f"numeric_kernel_{args.workload}.md", src_hash)
     value = world * L * (1 + NUMERIC_STEPS) / (ms / 1e3) / 1e9
 
