@@ -366,12 +366,13 @@ typedef struct fsparse_config {
    then the tuned table, then built-in defaults. */
 fsparse_status fsparse_get_config(int64_t len, int32_t m, int32_t n, fsparse_config *out);
 
-/* Per-phase device time of the calling thread's last symbolic or assemble
-   call, recorded when FSPARSE_TIMING=1 is set for that call (CUDA events on
+/* Per-phase device time of the calling thread's last symbolic, assemble or
+   append call, recorded when FSPARSE_TIMING=1 is set for that call (CUDA events on
    its stream, read at its final synchronisation; a call made without it
    records nothing).  Writes up to `max` phase names
    (static strings, e.g. "bucket_count", "bucket_scatter", "bucket_emit",
-   "digit_hist", "digit_passes", "emit", "jcS_scan", "numeric_fold") and
+   "digit_hist", "digit_passes", "emit", "jcS_scan", "numeric_fold"; an
+   append adds "append_symbolic" and the "merge_*" phases) and
    durations in ms; returns the number of phases recorded (0 when none).
    Either array may be NULL.  Host only. */
 int32_t fsparse_last_timings(const char **names, double *ms, int32_t max);

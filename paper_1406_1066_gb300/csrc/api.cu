@@ -761,9 +761,12 @@ fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const i
     if (cur != a.device) return set_error(FSPARSE_ERR_ARG, "the plan belongs to another device");
 
     // The new triplets alone, checked against the plan's dimensions.
+    TimerScope timing(s);
+    PhaseRangeGuard phase_guard_;
     Plan *b = nullptr;
     fsparse_status e = symbolic_impl(ii, jj, nullptr, nullptr, len, a.m, a.n, 0, s, &b, nullptr);
     if (e != FSPARSE_OK) return e;
+    phase_mark("append_symbolic");
 
     Plan *out = new (std::nothrow) Plan();
     if (!out) {
@@ -807,6 +810,7 @@ fsparse_status fsparse_plan_append(fsparse_plan plan, const int32_t *ii, const i
     if (h_st.oob) return fail(set_error(FSPARSE_ERR_INTERNAL, "internal index check failed"));
     out->nnz = out->len ? (int64_t)h_st.nnz : 0;
     out->cap = out->nnz;
+    timing.finish();
     free_plan_arrays_on(*b, s);
     delete b;
     *plan_out = reinterpret_cast<fsparse_plan>(out);

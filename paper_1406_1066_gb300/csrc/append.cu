@@ -244,6 +244,7 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
         (e = scratch.get(&mvA, (size_t)na + 1)) || (e = scratch.get(&mvB, (size_t)nb + 1)))
         return e;
     // run starts (an empty side has rs = {0})
+    phase_begin("merge_run_starts");
     if (a.len > 0) {
         run_starts_kernel<<<grid_for(a.nchunks), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, a.nchunks, rsA);
         FSP_LAUNCHED();
@@ -256,12 +257,16 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
     } else {
         FSP_CUDA(cudaMemsetAsync(rsB, 0, 4, s));
     }
+    phase_mark("merge_run_starts");
+    phase_begin("merge_columns");
     if (na + nb > 0) {
         const int cgrid = (int)std::max<int64_t>(
             1, std::min<int64_t>((a.n + kColThreads - 1) / kColThreads, (int64_t)sm_count(0) * 16));
         merge_columns_kernel<<<cgrid, kColThreads, 0, s>>>(a.jcS, a.irS, b.jcS, b.irS, a.n, lbA, eqA, lbB, eqB);
         FSP_LAUNCHED();
     }
+    phase_mark("merge_columns");
+    phase_begin("merge_slots");
     if ((e = exclusive_scan_u32(eqA, shA, na, st, scratch, s)) != FSPARSE_OK) return e;
     if ((e = exclusive_scan_u32(eqB, shB, nb, st, scratch, s)) != FSPARSE_OK) return e;
     if (na > 0) {
@@ -284,6 +289,8 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
         merge_shift_kernel<<<grid_for(nb), 256, 0, s>>>(nb, lbB, eqB, rsA, 1, mvB);
         FSP_LAUNCHED();
     }
+    phase_mark("merge_slots");
+    phase_begin("merge_positions");
     if (a.len > 0) {
         merge_positions_kernel<<<grid_for((a.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(
             a.perm, a.chunk_slot0, a.len, na, mvA, 0u, out.perm, out.len, st);
@@ -294,6 +301,8 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
             b.perm, b.chunk_slot0, b.len, nb, mvB, (uint32_t)a.len, out.perm, out.len, st);
         FSP_LAUNCHED();
     }
+    phase_mark("merge_positions");
+    phase_begin("merge_chunk_heads");
     // chunk slot bases of the merged order; nnz = na + nb - shared
     uint32_t *counts;
     if ((e = scratch.get(&counts, (size_t)out.nchunks + 1)) != FSPARSE_OK) return e;
@@ -302,7 +311,9 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
                                                                              counts);
         FSP_LAUNCHED();
     }
-    return exclusive_scan_u32(counts, out.chunk_slot0, out.nchunks, st, scratch, s);
+    e = exclusive_scan_u32(counts, out.chunk_slot0, out.nchunks, st, scratch, s);
+    phase_mark("merge_chunk_heads");
+    return e;
 }
 
 }  // namespace fsp
