@@ -155,6 +155,44 @@ __global__ void merge_shift_kernel(int64_t nnz, const uint32_t *__restrict__ lb,
     }
 }
 
+// Start of run x of a plan (its first position in the sorted order), found
+// from the plan's chunk slot bases instead of a pass over all its runs: the
+// chunk q with chunk_slot0[q] <= x < chunk_slot0[q + 1] holds the head, as the
+// (x - chunk_slot0[q])-th head of that chunk; x == nnz gives len.
+__device__ __forceinline__ uint32_t run_start_of(const uint32_t *__restrict__ perm,
+                                                 const uint32_t *__restrict__ chunk_slot0, int64_t len,
+                                                 int64_t nchunks, int64_t nnz, uint32_t x) {
+    if (x >= nnz) return (uint32_t)len;
+    int64_t lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(chunk_slot0 + mid) <= x) lo = mid; else hi = mid - 1;
+    }
+    uint32_t need = x - __ldg(chunk_slot0 + lo);
+    const int64_t p1 = min64((lo + 1) * kChunk, len);
+    for (int64_t p = lo * kChunk; p < p1; ++p) {
+        if (__ldg(perm + p) & kHeadBit) {
+            if (need == 0) return (uint32_t)p;
+            --need;
+        }
+    }
+    return (uint32_t)len;   // only for a damaged plan
+}
+
+// The new side's shifts when it has few runs: the old side's run starts are
+// looked up where they are needed instead of being listed for all old runs.
+__global__ void merge_shift_search_kernel(int64_t nnz, const uint32_t *__restrict__ lb,
+                                          const uint32_t *__restrict__ eq, const uint32_t *__restrict__ other_perm,
+                                          const uint32_t *__restrict__ other_cs0, int64_t other_len,
+                                          int64_t other_nchunks, int64_t other_nnz, uint32_t *__restrict__ shift) {
+    for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < nnz;
+         y += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t e = eq[y];
+        shift[y] = run_start_of(other_perm, other_cs0, other_len, other_nchunks, other_nnz, lb[y] + e) |
+                   (e ? kHeadBit : 0u);
+    }
+}
+
 // Positions of one side's runs in the merged order, one thread per position
 // (a warp takes 32 consecutive positions, two chunks, so loads and stores
 // are coalesced and the lanes of one run share their lookups).  The slot of
@@ -166,7 +204,8 @@ constexpr int kGroups = 4;
 
 __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ chunk_slot0,
                                        int64_t len, int64_t nnz, const uint32_t *__restrict__ shift,
-                                       uint32_t kofs, uint32_t *__restrict__ out, int64_t len_out, DevStatus *st) {
+                                       uint32_t kofs, uint32_t *__restrict__ out, int64_t len_out,
+                                       uint32_t *__restrict__ head_counts, int64_t nchunks_out, DevStatus *st) {
     const int lane = threadIdx.x & 31;
     const uint32_t le = lanemask_lt() | (1u << lane);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -192,29 +231,32 @@ __global__ void merge_positions_kernel(const uint32_t *__restrict__ perm, const 
 #pragma unroll
         for (int g = 0; g < kGroups; ++g) {
             const int64_t p = w0 + 32 * g + lane;
+            const int64_t t = p + (sh[g] & kIndexMask);
+            const bool keep = ok[g] && (x[g] & kHeadBit) && !(sh[g] & kHeadBit);
             if (!ok[g]) {
                 if (p < len) atomicOr(&st->oob, 1u);
-                continue;
+            } else if (in_range(t, len_out, st)) {
+                out[t] = ((x[g] & kIndexMask) + kofs) | (keep ? kHeadBit : 0u);
             }
-            const int64_t t = p + (sh[g] & kIndexMask);
-            const bool keep = (x[g] & kHeadBit) && !(sh[g] & kHeadBit);
-            if (in_range(t, len_out, st)) out[t] = ((x[g] & kIndexMask) + kofs) | (keep ? kHeadBit : 0u);
+            // Run heads per chunk of the merged order, counted here instead of
+            // in a pass over the merged perm: the kept heads of the warp come
+            // in ascending merged position, so heads that land in one chunk
+            // are neighbours among them and add their count once.
+            const uint32_t hm = __ballot_sync(0xffffffffu, keep);
+            if (hm) {
+                const uint32_t key = (uint32_t)(t >> kChunkShift);
+                const uint32_t before = hm & lanemask_lt();
+                const int prev = before ? 31 - __clz(before) : lane;
+                const uint32_t prev_key = __shfl_sync(0xffffffffu, key, prev);
+                const uint32_t lm = __ballot_sync(0xffffffffu, keep && (!before || prev_key != key));
+                if (keep && ((lm >> lane) & 1u)) {
+                    const uint32_t above = lm & ~((2u << lane) - 1u);
+                    const uint32_t upto = above ? (1u << (__ffs(above) - 1)) - 1u : 0xffffffffu;
+                    const uint32_t c = __popc(hm & upto & ~((1u << lane) - 1u));
+                    if (in_range(key, nchunks_out, st)) atomicAdd(head_counts + key, c);
+                }
+            }
         }
-    }
-}
-
-// Run heads per chunk of the merged order (a warp counts two chunks).
-__global__ void merged_chunk_heads_kernel(const uint32_t *__restrict__ perm, int64_t len, int64_t nchunks,
-                                          uint32_t *__restrict__ counts) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < len;
-         w0 += warps * 32) {
-        const int64_t p = w0 + lane;
-        const bool head = p < len && (__ldg(perm + p) & kHeadBit) != 0;
-        const uint32_t hm = __ballot_sync(0xffffffffu, head);
-        const int64_t q = (w0 >> kChunkShift) + (lane >> 4);
-        if ((lane & 15) == 0 && q < nchunks) counts[q] = __popc(hm & (0xffffu << (lane & 16)));
     }
 }
 
@@ -243,12 +285,14 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
         (e = scratch.get(&shA, (size_t)na + 1)) || (e = scratch.get(&shB, (size_t)nb + 1)) ||
         (e = scratch.get(&mvA, (size_t)na + 1)) || (e = scratch.get(&mvB, (size_t)nb + 1)))
         return e;
-    // run starts (an empty side has rs = {0})
+    // run starts (an empty side has rs = {0}); the old side's are listed only
+    // when the new side has many runs, else looked up where needed
+    const bool search_a = nb * 64 < na;
     phase_begin("merge_run_starts");
-    if (a.len > 0) {
+    if (a.len > 0 && !search_a) {
         run_starts_kernel<<<grid_for(a.nchunks), 256, 0, s>>>(a.perm, a.chunk_slot0, a.len, a.nchunks, rsA);
         FSP_LAUNCHED();
-    } else {
+    } else if (a.len == 0) {
         FSP_CUDA(cudaMemsetAsync(rsA, 0, 4, s));
     }
     if (b.len > 0) {
@@ -285,32 +329,33 @@ fsparse_status append_merge(const Plan &a, const Plan &b, Plan &out, DevStatus *
         merge_shift_kernel<<<grid_for(na), 256, 0, s>>>(na, lbA, eqA, rsB, 0, mvA);
         FSP_LAUNCHED();
     }
-    if (nb > 0) {
+    if (nb > 0 && search_a && a.len > 0) {
+        merge_shift_search_kernel<<<grid_for(nb), 256, 0, s>>>(nb, lbB, eqB, a.perm, a.chunk_slot0, a.len,
+                                                               a.nchunks, na, mvB);
+        FSP_LAUNCHED();
+    } else if (nb > 0) {
         merge_shift_kernel<<<grid_for(nb), 256, 0, s>>>(nb, lbB, eqB, rsA, 1, mvB);
         FSP_LAUNCHED();
     }
     phase_mark("merge_slots");
     phase_begin("merge_positions");
+    // run heads per chunk of the merged order, counted by the position kernels
+    uint32_t *counts;
+    if ((e = scratch.get(&counts, (size_t)out.nchunks + 1)) != FSPARSE_OK) return e;
+    FSP_CUDA(cudaMemsetAsync(counts, 0, ((size_t)out.nchunks + 1) * 4, s));
     if (a.len > 0) {
         merge_positions_kernel<<<grid_for((a.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(
-            a.perm, a.chunk_slot0, a.len, na, mvA, 0u, out.perm, out.len, st);
+            a.perm, a.chunk_slot0, a.len, na, mvA, 0u, out.perm, out.len, counts, out.nchunks, st);
         FSP_LAUNCHED();
     }
     if (b.len > 0) {
         merge_positions_kernel<<<grid_for((b.len + 8 * kGroups - 1) / (8 * kGroups)), 256, 0, s>>>(
-            b.perm, b.chunk_slot0, b.len, nb, mvB, (uint32_t)a.len, out.perm, out.len, st);
+            b.perm, b.chunk_slot0, b.len, nb, mvB, (uint32_t)a.len, out.perm, out.len, counts, out.nchunks, st);
         FSP_LAUNCHED();
     }
     phase_mark("merge_positions");
     phase_begin("merge_chunk_heads");
     // chunk slot bases of the merged order; nnz = na + nb - shared
-    uint32_t *counts;
-    if ((e = scratch.get(&counts, (size_t)out.nchunks + 1)) != FSPARSE_OK) return e;
-    if (out.len > 0) {
-        merged_chunk_heads_kernel<<<grid_for((out.len + 7) / 8), 256, 0, s>>>(out.perm, out.len, out.nchunks,
-                                                                             counts);
-        FSP_LAUNCHED();
-    }
     e = exclusive_scan_u32(counts, out.chunk_slot0, out.nchunks, st, scratch, s);
     phase_mark("merge_chunk_heads");
     return e;

@@ -343,9 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         for (int i = 0; i < IPT; ++i) {
             if (valid[i]) {
                 const uint32_t r = (uint32_t)((pk[i] >> kb) & ((1ull << rb) - 1)) - row_lo;
-                // most rows repeat inside a bucket: read first, and only set a
-                // missing bit (a racing duplicate set is harmless)
-                if (!(s_bits[r >> 5] & (1u << (r & 31)))) atomicOr(&s_bits[r >> 5], 1u << (r & 31));
+                atomicOr(&s_bits[r >> 5], 1u << (r & 31));
             }
         }
         __syncthreads();
@@ -400,7 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                 const uint32_t rank = s_pref[roff >> 5] + __popc(s_bits[roff >> 5] & ((1u << (roff & 31)) - 1u));
                 const uint32_t kk = (uint32_t)(w >> (kb + rb)) * R + rank;
                 if (in_range(kk, K, a.st)) {
-                    if (!(s_kb[kk >> 5] & (1u << (kk & 31)))) atomicOr(&s_kb[kk >> 5], 1u << (kk & 31));
+                    atomicOr(&s_kb[kk >> 5], 1u << (kk & 31));
                     pk[i] = (w & kmask) | ((uint64_t)kk << 30) | ((uint64_t)roff << 46);
                 }
             }
@@ -445,52 +443,34 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             }
         }
         __syncthreads();
-        // First position of every run: exclusive scan of the run sizes.  The
-        // triplets are grouped by slot in a staging order that keeps runs of
-        // up to 4, of 5 to 8, and of more triplets apart (s_klo: staging start
-        // of every run), so the lanes of a warp mostly rank runs of one length
-        // class below; s_klo lives in the row-rank prefix, free by now, when
-        // the runs fit it (otherwise the staging order is the CCS order).
-        uint16_t *s_klo = s_pref;
-        const bool classed = U <= (uint32_t)(kRowBits / 32);
+        // First position of every run: exclusive scan of the run sizes.  (Laying
+        // the runs out by length class for the in-run k rank below measured no
+        // faster: the rank's cost is not the lanes' unequal run lengths.)
         {
-            // (the run sizes are read twice from shared memory rather than
-            // kept in registers, which the packed words already fill)
-            auto cls_of = [](uint32_t c) { return (c <= 4u ? c : 0u) | ((c > 4u && c <= 8u ? c : 0u) << 16); };
-            uint32_t sum = 0, packed = 0;
+            uint32_t c[IPT], sum = 0;
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const int r = tid * IPT + j;
-                const uint32_t c = r < (int)U ? s_cnt[r] : 0u;
-                sum += c;
-                packed += cls_of(c);
+                c[j] = r < (int)U ? s_cnt[r] : 0u;
+                sum += c[j];
             }
-            uint32_t tot, ptot = 0;
+            uint32_t tot;
             uint32_t run = block_exclusive_scan<THREADS>(sum, s_scan, &tot);
-            uint32_t pe = classed ? block_exclusive_scan<THREADS>(packed, s_scan, &ptot) : 0u;
-            const uint32_t T0 = ptot & 0xffffu, T1 = ptot >> 16;
-#pragma unroll 4
+#pragma unroll
             for (int j = 0; j < IPT; ++j) {
                 const int r = tid * IPT + j;
-                if (r >= (int)U) break;
-                const uint32_t c = s_cnt[r];
-                if (classed) {
-                    const uint32_t e0 = pe & 0xffffu, e1 = pe >> 16;
-                    s_klo[r] = (uint16_t)(c <= 4u ? e0 : c <= 8u ? T0 + e1 : T0 + T1 + (run - e0 - e1));
-                    pe += cls_of(c);
-                }
-                s_lo[r] = (uint16_t)run;
-                run += c;
+                if (r < (int)U) s_lo[r] = (uint16_t)run;
+                run += c[j];
             }
             if (tid == 0) s_lo[U] = (uint16_t)nx;
         }
         __syncthreads();
-        // Group the triplets by slot (staging order).
+        // Group the triplets by slot.
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             if (pk[i] != ~0ull) {
                 const uint32_t slot = (uint32_t)(pk[i] >> 30) & 0x1fffu;
-                const uint32_t q = (classed ? s_klo[slot] : s_lo[slot]) + (uint32_t)(pk[i] >> 43);
+                const uint32_t q = s_lo[slot] + (uint32_t)(pk[i] >> 43);
                 if (in_range(q, nx, a.st)) {
                     s_k[q] = (uint32_t)(pk[i] & kmask);
                     s_slot[q] = (uint16_t)slot;
@@ -521,23 +501,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             const uint32_t kq = s_k[q], slot = s_slot[q];
             if (!in_range(slot, U, a.st)) continue;
             const int lo = s_lo[slot], hi = s_lo[slot + 1];
-            int dest = lo;
+            int dest = q;
             if (hi - lo > 1) {
                 if (hi - lo > kRunSortMax) {
                     atomicOr(&a.st->overflow, 1u);   // redone by the onesweep path
-                    dest = q;
                 } else {
-                    // The run's staged k, by 16-byte loads from the aligned
-                    // word at or below its staging start sb; entries outside
-                    // [sb, sb + len) are masked out (they stay inside the
-                    // shared array: sb + len + 3 <= CAP + 3 words lands in the
-                    // next region at worst).
-                    const int sb = classed ? s_klo[slot] : lo;
+                    // 16-byte loads from the aligned word at or below lo;
+                    // entries outside [lo, hi) are masked out (they stay
+                    // inside the shared array: hi + 3 <= CAP + 3 words lands
+                    // in the next region at worst).
                     const uint32_t len = (uint32_t)(hi - lo);
                     int rank = 0;
-                    for (int r = sb & ~3; r < sb + (int)len; r += 4) {
+                    for (int r = lo & ~3; r < hi; r += 4) {
                         const uint4 f = *reinterpret_cast<const uint4 *>(s_k + r);
-                        const uint32_t o = (uint32_t)(r - sb);
+                        const uint32_t o = (uint32_t)(r - lo);
                         rank += ((o < len) & (f.x < kq)) + ((o + 1 < len) & (f.y < kq)) +
                                 ((o + 2 < len) & (f.z < kq)) + ((o + 3 < len) & (f.w < kq));
                     }

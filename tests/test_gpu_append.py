@@ -33,10 +33,21 @@ def append_parts(t, cuts):
     return plan
 
 
-@pytest.mark.parametrize("split", [0.0, 0.01, 0.5, 0.93, 1.0])
+@pytest.mark.parametrize("split", [0.0, 0.01, 0.5, 0.93, 0.995, 1.0])
 def test_append_random(split):
     t = inputs.random_small(40_000, 500, 400, 51, dup=0.5)
     plan = append_parts(t, [int(t.L * split)])
+    check_plan(plan, t.ii, t.jj, t.s, t.m, t.n)
+
+
+@pytest.mark.parametrize("frac", [0.01, 0.002])
+def test_append_small_part_of_a_mesh(frac):
+    """A small appended part: the old plan's run starts are looked up where
+    the new runs need them instead of being listed (fewer new runs than 1/64
+    of the old ones)."""
+    t = inputs.mesh3d(20, 56)
+    cut = t.L - int(t.L * frac)
+    plan = append_parts(t, [cut])
     check_plan(plan, t.ii, t.jj, t.s, t.m, t.n)
 
 
