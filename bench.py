@@ -650,10 +650,11 @@ def gpu_arm(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        sec, Ls = oracle_job(t, 4 if t.L > 10**7 else 1, NUMERIC_STEPS)
+        # one whole step of the workload (about 10 s on the machine's host cores)
+        sec, Ls = oracle_job(t, 1, NUMERIC_STEPS)
         cpu = {"value": Ls * (1 + NUMERIC_STEPS) / sec / 1e9, "unit": "G triplets/s", "cores": 1,
                "kind": "oracle", "seconds": sec,
-               "sample": f"first {Ls} triplets (1/4 of the cube, element order): one oracle assembly "
+               "sample": f"one step of the whole workload ({Ls} triplets): one oracle assembly "
                          f"+ {NUMERIC_STEPS} oracle numeric passes, single thread"}
 
     paper_cpu = None

@@ -1,5 +1,11 @@
 // rank.cuh -- stable block-local ranking of radix digits.
 //
+// The technique is the published one of the Onesweep radix sort (Adinets and
+// Merrill, "Onesweep: a faster least significant digit radix sort for GPUs",
+// 2022): find the lanes of a warp that hold the same digit, rank each item
+// among its earlier peers, keep running counts per (warp, digit).  The code
+// below is written for this library, with its own peer and counter protocol.
+//
 // Items are held warp-striped: item i of lane l in warp w sits at block
 // position w*32*ITEMS + i*32 + l, so visiting (warp, i, lane) in order
 // visits positions in order.  For every item the warp finds its peers (the
