@@ -215,10 +215,12 @@ void note_use(UseLog &log, cudaStream_t s) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
         cudaGetLastError();
+        std::lock_guard<std::mutex> lock(log.mu);
         log.overflow = true;
         return;
     }
     if (cap != cudaStreamCaptureStatusNone) return;   // graph replays are the caller's to finish
+    std::lock_guard<std::mutex> lock(log.mu);
     int i = 0;
     while (i < log.n && log.stream[i] != s) ++i;
     if (i == log.n) {
@@ -284,7 +286,8 @@ static void release_after(void *const *ptrs, int count, UseLog &log, cudaStream_
     }
     if (tail) cudaEventDestroy(tail);   // released by the driver once it has completed
     for (int i = 0; i < log.n; ++i) cudaEventDestroy(log.event[i]);
-    log = UseLog{};
+    log.n = 0;
+    log.overflow = false;
     cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -22,6 +23,7 @@ struct DevStatus;
 // a capture belongs to the graph); replays are the caller's to finish.
 struct UseLog {
     static constexpr int kMax = 8;
+    std::mutex mu;           // numeric calls on one plan may come from several host threads
     cudaStream_t stream[kMax] = {};
     cudaEvent_t event[kMax] = {};
     int n = 0;
