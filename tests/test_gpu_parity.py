@@ -227,3 +227,39 @@ def test_destroy_with_work_in_flight(strategy):
     jcS, irS, prS, plan = fsparse.assemble(ii_d, jj_d, vals[2], t.m, t.n)
     assert np.array_equal(bits(prS[:nnz].cpu().numpy()), bits(ref.prS))
     plan.close()
+
+
+def test_release_after_launches_on_side_streams():
+    """Numeric launches on two non-blocking streams, from two host threads at
+    once, then the plan is released right away: the release waits (on the
+    GPU) for both streams' recorded launches, so the results are exact and
+    nothing faults, and the memory it frees is reused safely afterwards."""
+    import threading
+
+    t = inputs.mesh3d(30, 18)
+    ii_d, jj_d = to_dev(t.ii), to_dev(t.jj)
+    vals = [inputs.mesh_values(t.L, 60 + k) for k in range(2)]
+    refs = [oracle.assemble(t.ii, t.jj, v, t.m, t.n).prS for v in vals]
+    plan = fsparse.symbolic(ii_d, jj_d, t.m, t.n)
+    streams = [torch.cuda.Stream(device=DEV) for _ in range(2)]
+    vd = [to_dev(v) for v in vals]
+    outs = [[torch.empty(plan.cap, dtype=torch.float64, device=DEV) for _ in range(8)] for _ in range(2)]
+    torch.cuda.synchronize()
+
+    def work(w):
+        with torch.cuda.stream(streams[w]):
+            for o in outs[w]:
+                fsparse.numeric(plan, vd[w], o)
+
+    threads = [threading.Thread(target=work, args=(w,)) for w in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    plan.close()   # no synchronisation before it
+    junk = torch.full((plan.len * 2,), -1, dtype=torch.int32, device=DEV)   # likely reuses freed blocks
+    torch.cuda.synchronize()
+    for w in range(2):
+        for o in outs[w]:
+            assert np.array_equal(bits(o.cpu().numpy()), bits(refs[w]))
+    del junk
