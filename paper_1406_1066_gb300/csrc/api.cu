@@ -155,6 +155,7 @@ int injected_fault() {
     if (std::strcmp(f, "alloc") == 0) return FAULT_ALLOC;
     if (std::strcmp(f, "timeout") == 0) return FAULT_TIMEOUT;
     if (std::strcmp(f, "timeout_sort") == 0) return FAULT_TIMEOUT_SORT;
+    if (std::strcmp(f, "index") == 0) return FAULT_INDEX;
     return FAULT_NONE;
 }
 
@@ -419,6 +420,11 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
     } else {
         e = run_symbolic(ii, jj, sr, prS, len, *plan, cfg, d_st, scratch, s, &folded);
         if (e != FSPARSE_OK) return fail(e);
+    }
+    if (injected_fault() == FAULT_INDEX) {   // seed the status word as a kernel finding a bad index would
+        const uint32_t one = 1;
+        if (cudaMemcpyAsync(&d_st->bad_index, &one, 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "cudaMemcpyAsync"));
     }
     if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
     if (h_st.overflow && !h_st.bad_index && !h_st.timeout) {

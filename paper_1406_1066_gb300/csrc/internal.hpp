@@ -102,9 +102,11 @@ fsparse_status cuda_error(cudaError_t e, const char *what);
 // look-back scan withhold its prefix, so the following tiles' bounded waits
 // run out and the call returns FSPARSE_ERR_TIMEOUT; FSPARSE_FAULT=timeout_sort
 // does the same in the first digit pass of the onesweep sort, so that pass
-// leaves some positions unwritten and the kernels after it read stale keys.
+// leaves some positions unwritten and the kernels after it read stale keys;
+// FSPARSE_FAULT=index seeds the device status word with a bad index after the
+// symbolic kernels, so the call takes its bad-index return on valid input.
 // Nothing faults, traps or hangs the GPU; unset, it costs one getenv per call.
-enum InjectedFault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2, FAULT_TIMEOUT_SORT = 3 };
+enum InjectedFault { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_TIMEOUT = 2, FAULT_TIMEOUT_SORT = 3, FAULT_INDEX = 4 };
 int injected_fault();
 
 // Per-phase timing of one symbolic call with CUDA events on its stream, on

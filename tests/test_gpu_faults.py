@@ -24,6 +24,20 @@ def test_injected_allocation_failure(monkeypatch):
     assert_same(gpu_assemble(t.ii, t.jj, t.s, t.m, t.n), oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
 
 
+def test_injected_bad_index(monkeypatch):
+    """FSPARSE_FAULT=index seeds the status word: a valid input takes the
+    bad-index return (no plan), and the next call is exact."""
+    t = inputs.random_small(6000, 70, 50, 76, dup=0.3)
+    monkeypatch.setenv("FSPARSE_FAULT", "index")
+    for strategy in (1, 2):
+        with config(strategy=strategy):
+            with pytest.raises(fsparse.FsparseError) as e:
+                fsparse.assemble(to_dev(t.ii), to_dev(t.jj), to_dev(t.s), t.m, t.n)
+            assert e.value.status == fsparse.ERR_INDEX
+    monkeypatch.delenv("FSPARSE_FAULT")
+    assert_same(gpu_assemble(t.ii, t.jj, t.s, t.m, t.n), oracle.assemble(t.ii, t.jj, t.s, t.m, t.n))
+
+
 def test_injected_lookback_timeout(monkeypatch):
     """The column-pointer scan of the onesweep path spans several tiles
     (8000 columns); with tile 0 withheld the others wait out their bound."""
