@@ -140,9 +140,13 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
                                       int64_t len, int32_t m, int32_t n, int rb, int cs, int kb,
                                       int nb, const uint32_t *__restrict__ goff,
                                       const uint32_t *__restrict__ bstart, uint64_t *__restrict__ words,
-                                      DevStatus *st) {
+                                      const uint32_t *__restrict__ largest, DevStatus *st) {
     extern __shared__ uint32_t s_cur[];
     const int tid = threadIdx.x;
+    // The host redoes count and scatter with narrower buckets when the
+    // largest one is over the emit's capacity; this width's scatter is then
+    // skipped (it was queued before the host knew).
+    if (*largest > (uint32_t)kMaxBucketCap) return;
     const int64_t g = blockIdx.x, G = gridDim.x;
     for (int b = tid; b < nb; b += blockDim.x) s_cur[b] = bstart[b] + goff[g * nb + b];
     __syncthreads();
@@ -822,7 +826,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
         FSP_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
         bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
-                                                     words, st);
+                                                     words, dmax, st);
         FSP_LAUNCHED();
         phase_mark("bucket_scatter");
         FSP_CUDA(cudaEventSynchronize(got_largest));

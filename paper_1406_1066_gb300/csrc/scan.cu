@@ -24,13 +24,25 @@ __global__ void __launch_bounds__(THREADS)
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t p0 = tile * TILE + (int64_t)tid * ITEMS;
+    static_assert(ITEMS % 4 == 0, "16-byte groups");
     uint32_t v[ITEMS];
     uint32_t sum = 0;
+    const bool whole = p0 + ITEMS <= count;
+    if (whole && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        v[i] = p0 + i < count ? in[p0 + i] : 0u;
-        sum += v[i];
+        for (int q = 0; q < ITEMS / 4; ++q) {
+            const uint4 x = reinterpret_cast<const uint4 *>(in + p0)[q];
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) v[i] = p0 + i < count ? in[p0 + i] : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) sum += v[i];
     uint32_t tile_sum;
     const uint32_t mine = block_exclusive_scan<THREADS>(sum, s_scan, &tile_sum);
     if (tid < 32) {
@@ -47,20 +59,37 @@ __global__ void __launch_bounds__(THREADS)
     }
     __syncthreads();
     uint32_t run = s_excl + mine;
+    if (whole && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const int64_t p = p0 + i;
-        if (p < count) {
-            out[p] = run;
-            run += v[i];
-            if (p == count - 1) out[count] = run;
+        for (int q = 0; q < ITEMS / 4; ++q) {
+            uint4 y;
+            y.x = run;
+            run += v[4 * q];
+            y.y = run;
+            run += v[4 * q + 1];
+            y.z = run;
+            run += v[4 * q + 2];
+            y.w = run;
+            run += v[4 * q + 3];
+            reinterpret_cast<uint4 *>(out + p0)[q] = y;
+        }
+        if (p0 + ITEMS == count) out[count] = run;
+    } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int64_t p = p0 + i;
+            if (p < count) {
+                out[p] = run;
+                run += v[i];
+                if (p == count - 1) out[count] = run;
+            }
         }
     }
 }
 
 fsparse_status exclusive_scan_u32(const uint32_t *counts, uint32_t *out, int64_t count,
                                   DevStatus *st, Scratch &scratch, cudaStream_t s) {
-    constexpr int THREADS = 256, ITEMS = 8, TILE = THREADS * ITEMS;
+    constexpr int THREADS = 256, ITEMS = 16, TILE = THREADS * ITEMS;
     if (count == 0) {
         FSP_CUDA(cudaMemsetAsync(out, 0, 4, s));
         return FSPARSE_OK;
