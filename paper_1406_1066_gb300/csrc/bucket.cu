@@ -5,10 +5,11 @@
 // as long as the matrix is wide or tall.  On a GPU the cheap counting pass is
 // the one whose table fits in shared memory, so the column index is split:
 //
-//   bucket = (j-1) >> cs            (up to 32768 buckets, 2^cs columns each)
+//   bucket = (j-1) >> cs            (up to 131072 buckets, 2^cs columns each)
 //
 //   1. count:    every block counts bucket sizes over its contiguous slice of
-//                jj in a shared-memory table;
+//                jj in a shared-memory table (above 32768 buckets, one pass
+//                per range of 32768 buckets, each skipping the others);
 //   2. offsets:  every non-empty (block, bucket) count reserves its range
 //                inside the bucket by one atomic add on the bucket's total,
 //                then an exclusive scan over buckets gives the bucket starts;
@@ -43,7 +44,9 @@
 
 namespace fsp {
 
-constexpr int64_t kMaxBuckets = 32768;
+constexpr int64_t kBucketsPerPass = 32768;   // shared-memory table of the count and scatter kernels
+constexpr int kMaxBucketPasses = 4;           // more buckets: the count and scatter run once per range
+constexpr int64_t kMaxBuckets = kBucketsPerPass * kMaxBucketPasses;
 constexpr int kMaxColBits = 12;     // 2^cs column counters in shared memory
 constexpr int kRunSortMax = 128;    // longest run put back into k order in the bucket kernel
 constexpr int kRowBits = 1 << 16;   // row ranges up to this are compressed to dense ranks
@@ -93,7 +96,7 @@ bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fspars
 //      the blocks inside a bucket is therefore arbitrary, as is the order
 //      inside a block's range: the emit kernel restores ascending k.
 __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len, int32_t n, int cs,
-                                    int nb, uint32_t *__restrict__ goff, uint32_t *__restrict__ tot,
+                                    int b_lo, int nb, uint32_t *__restrict__ goff, uint32_t *__restrict__ tot,
                                     uint32_t *largest, DevStatus *st) {
     extern __shared__ uint32_t s_h[];
     const int tid = threadIdx.x;
@@ -103,7 +106,11 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len,
     const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
     // (Counting runs of equal buckets across the lanes first, one add per
     // run, measured slower here: 0.18 against 0.13 ms on the 100^3 cube.)
-    auto count = [&](int32_t j) { atomicAdd(&s_h[(uint32_t)(checked_index(j, n, st) - 1) >> cs], 1u); };
+    // buckets [b_lo, b_lo + nb) only; the others belong to another pass
+    auto count = [&](int32_t j) {
+        const uint32_t b = ((uint32_t)(checked_index(j, n, st) - 1) >> cs) - (uint32_t)b_lo;
+        if (b < (uint32_t)nb) atomicAdd(&s_h[b], 1u);
+    };
     // scalar head up to a 16-byte boundary, int4 body, scalar tail
     const int64_t v0 = min64(c1, (c0 + 3) & ~int64_t(3)), v1 = max(v0, c1 & ~int64_t(3));
     if (((reinterpret_cast<uintptr_t>(jj)) & 15) == 0) {
@@ -124,7 +131,7 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len,
     for (int b = tid; b < nb; b += blockDim.x) {
         const uint32_t c = s_h[b];
         if (c) {
-            const uint32_t old = atomicAdd(&tot[b], c);
+            const uint32_t old = atomicAdd(&tot[b_lo + b], c);
             goff[g * nb + b] = old;
             m = max(m, old + c);
         }
@@ -138,7 +145,7 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len,
 //    not kept; the emit kernel restores ascending k inside each run).
 __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *__restrict__ ii, const int32_t *__restrict__ jj,
                                       int64_t len, int32_t m, int32_t n, int rb, int cs, int kb,
-                                      int nb, const uint32_t *__restrict__ goff,
+                                      int b_lo, int nb, const uint32_t *__restrict__ goff,
                                       const uint32_t *__restrict__ bstart, uint64_t *__restrict__ words,
                                       const uint32_t *__restrict__ largest, DevStatus *st) {
     extern __shared__ uint32_t s_cur[];
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
     // skipped (it was queued before the host knew).
     if (*largest > (uint32_t)kMaxBucketCap) return;
     const int64_t g = blockIdx.x, G = gridDim.x;
-    for (int b = tid; b < nb; b += blockDim.x) s_cur[b] = bstart[b] + goff[g * nb + b];
+    for (int b = tid; b < nb; b += blockDim.x) s_cur[b] = bstart[b_lo + b] + goff[g * nb + b];
     __syncthreads();
     const int64_t c0 = len * g / G, c1 = len * (g + 1) / G;
     const uint64_t lowmask = (1ull << cs) - 1;
@@ -160,7 +167,9 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
     auto put = [&](int32_t i, int32_t j, int64_t k, bool have) {
         const uint32_t i0 = have ? (uint32_t)(checked_index(i, m, st) - 1) : 0u;
         const uint32_t j0 = have ? (uint32_t)(checked_index(j, n, st) - 1) : 0u;
-        const uint32_t b = have ? j0 >> cs : 0xffff0000u | (uint32_t)lane;
+        const uint32_t bl = (j0 >> cs) - (uint32_t)b_lo;   // bucket inside this pass's range
+        have = have && bl < (uint32_t)nb;
+        const uint32_t b = have ? bl : 0xffff0000u | (uint32_t)lane;
         int head;
         uint32_t c;
         lane_runs(b, &head, &c);
@@ -806,7 +815,11 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
     uint32_t largest = 0;
     for (int attempt = 0;; ++attempt) {
         nb = (int)sh.nb;
-        const size_t table = (size_t)nb * 4;
+        // one count and one scatter pass per range of up to kBucketsPerPass
+        // buckets; each pass keeps only its range's table in shared memory
+        const int npass = (int)((nb + kBucketsPerPass - 1) / kBucketsPerPass);
+        const int nbp_max = (int)std::min<int64_t>(nb, kBucketsPerPass);
+        const size_t table = (size_t)nbp_max * 4;
         const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (200u << 10) / std::max<size_t>(table, 1)));
         G = sm_count(0) * per_sm;
         G = (int)std::max<int64_t>(1, std::min<int64_t>(G, (len + 4095) / 4096));
@@ -815,8 +828,12 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         FSP_CUDA(cudaMemsetAsync(tot, 0, (size_t)nb * 4, s));
         FSP_CUDA(cudaMemsetAsync(dmax, 0, 4, s));
         FSP_CUDA(cudaFuncSetAttribute(bucket_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
-        bucket_count_kernel<<<G, 1024, table, s>>>(jj, len, n, sh.cs, nb, goff, tot, dmax, st);
-        FSP_LAUNCHED();
+        for (int r = 0; r < npass; ++r) {
+            const int b_lo = r * (int)kBucketsPerPass, nbp = std::min(nb - b_lo, (int)kBucketsPerPass);
+            bucket_count_kernel<<<G, 1024, (size_t)nbp * 4, s>>>(jj, len, n, sh.cs, b_lo, nbp,
+                                                                 goff + (size_t)G * b_lo, tot, dmax, st);
+            FSP_LAUNCHED();
+        }
         FSP_CUDA(cudaMemcpyAsync(h_largest, dmax, 4, cudaMemcpyDeviceToHost, s));
         FSP_CUDA(cudaEventRecord(got_largest, s));
         phase_mark("bucket_count");
@@ -825,9 +842,12 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         FSP_CUDA(cudaMemsetAsync(ticket, 0, 4, s));
         if ((e = exclusive_scan_u32(tot, bstart, nb, st, scratch, s)) != FSPARSE_OK) return e;
         FSP_CUDA(cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)table));
-        bucket_scatter_kernel<<<G, 1024, table, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, nb, goff, bstart,
-                                                     words, dmax, st);
-        FSP_LAUNCHED();
+        for (int r = 0; r < npass; ++r) {
+            const int b_lo = r * (int)kBucketsPerPass, nbp = std::min(nb - b_lo, (int)kBucketsPerPass);
+            bucket_scatter_kernel<<<G, 1024, (size_t)nbp * 4, s>>>(ii, jj, len, m, n, key.rb, sh.cs, sh.kb, b_lo, nbp,
+                                                                   goff + (size_t)G * b_lo, bstart, words, dmax, st);
+            FSP_LAUNCHED();
+        }
         phase_mark("bucket_scatter");
         FSP_CUDA(cudaEventSynchronize(got_largest));
         largest = *h_largest;
