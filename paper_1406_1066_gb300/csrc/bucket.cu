@@ -822,9 +822,16 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
         const int npass = (int)((nb + kBucketsPerPass - 1) / kBucketsPerPass);
         const int nbp_max = (int)std::min<int64_t>(nb, kBucketsPerPass);
         const size_t table = (size_t)nbp_max * 4;
-        // two 1024-thread blocks fit an SM: a larger grid ran as a second,
-        // partial wave (count + scatter 0.44 -> 0.41 ms on the 100^3 cube at two)
-        const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2, (200u << 10) / std::max<size_t>(table, 1)));
+        // Blocks per SM (two 1024-thread blocks are resident at a time).  A
+        // large table is paid for by every block, so one wave of two per SM:
+        // count + scatter 0.42 ms on the 100^3 cube against 0.45-0.53 with
+        // 3-6.  With a small table more waves win where the triplets scatter
+        // (each wave's half-written lines then fit in L2): six per SM takes
+        // uniform random 2e7 from 0.50 to 0.35 ms and the pooled 2e7 from
+        // 0.48 to 0.32 ms.
+        const int per_sm_cap = table > (32u << 10) ? 2 : 6;
+        const int per_sm = (int)std::max<size_t>(
+            1, std::min<size_t>((size_t)per_sm_cap, (200u << 10) / std::max<size_t>(table, 1)));
         G = sm_count(0) * per_sm;
         G = (int)std::max<int64_t>(1, std::min<int64_t>(G, (len + 4095) / 4096));
         if ((e = scratch.get(&goff, (size_t)nb * G))) return e;
