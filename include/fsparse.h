@@ -37,6 +37,10 @@
  *     word that the host reads at the final synchronisation of the
  *     symbolic phase.  On error no plan is returned (*plan_out = NULL)
  *     unless stated otherwise, and output arrays hold unspecified values.
+ *   * The calls that synchronise their stream poll it (cudaStreamQuery)
+ *     for up to 10 ms before blocking in cudaStreamSynchronize, so that
+ *     they return within microseconds of the GPU finishing; the polling
+ *     thread stays busy meanwhile.
  *   * Entry points are thread-safe with respect to distinct plans.  Calls
  *     on one plan that overlap on the GPU (different streams, no ordering)
  *     are the caller's responsibility, like any other device buffer.

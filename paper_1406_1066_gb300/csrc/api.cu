@@ -203,11 +203,32 @@ static DevStatus *host_status() {
     return h;
 }
 
+// Wait for the stream's work: poll it for up to kPollMs, then block.  A
+// blocking wait returns some tens of microseconds after the GPU finishes
+// (the thread has to be woken), which the caller of a full assembly pays
+// once per call; polling returns within a microsecond or two.  Longer waits
+// block, so a long queue costs no more than kPollMs of host time.
+constexpr double kPollMs = 10.0;
+
+static fsparse_status wait_stream(cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaStreamQuery(s);
+        if (q == cudaSuccess) return FSPARSE_OK;
+        if (q != cudaErrorNotReady) return cuda_error(q, "cudaStreamQuery");
+        if (std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > kPollMs)
+            break;
+    }
+    FSP_CUDA(cudaStreamSynchronize(s));
+    return FSPARSE_OK;
+}
+
 static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) {
     DevStatus *h = host_status();
     if (!h) return set_error(FSPARSE_ERR_NOMEM, "cudaMallocHost failed");
     FSP_CUDA(cudaMemcpyAsync(h, d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    FSP_CUDA(cudaStreamSynchronize(s));
+    fsparse_status e = wait_stream(s);
+    if (e != FSPARSE_OK) return e;
     *out = *h;
     return FSPARSE_OK;
 }
