@@ -70,13 +70,14 @@ def test_key_bitmap_capacity(m):
     assert_same(g, oracle.assemble(ii, jj, s, m, n))
 
 
-def test_bucket_ranges_in_two_passes():
+@pytest.mark.parametrize("strategy", [2, 3])
+def test_bucket_ranges_in_two_passes(strategy):
     """2^21 + 2^18 columns x 16 triplets with a 1024-triplet bucket target:
     64 columns per bucket, 36864 buckets -- more than one shared-memory
     table holds, so the count and the scatter each run once per range of
     32768 buckets, every pass skipping the other range's triplets."""
     n, m = (1 << 21) + (1 << 18), 3000
     ii, jj, s = per_column(n, 16, m, 65)
-    with config(strategy=2, bucket_target=1024):
+    with config(strategy=strategy, bucket_target=1024):
         g = gpu_assemble(ii, jj, s, m, n)
     assert_same(g, oracle.assemble(ii, jj, s, m, n))
