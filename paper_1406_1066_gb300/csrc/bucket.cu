@@ -95,6 +95,15 @@ bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fspars
 //      final total passes through some block's old + count).  The order of
 //      the blocks inside a bucket is therefore arbitrary, as is the order
 //      inside a block's range: the emit kernel restores ascending k.
+// Zero-based index, clamped into [0, dim); an index below 1 or above dim
+// sets `bad` (reported once per thread).  The clamp keeps every address in
+// range, and both kernels map a bad index the same way.
+__device__ __forceinline__ uint32_t zero_based(int32_t v, int32_t dim, uint32_t &bad) {
+    const uint32_t z = (uint32_t)v - 1u;
+    bad |= (uint32_t)(z >= (uint32_t)dim);
+    return min(z, (uint32_t)dim - 1u);
+}
+
 template <bool RANGED>
 __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len, int32_t n, int cs,
                                     int b_lo, int nb, uint32_t *__restrict__ goff, uint32_t *__restrict__ tot,
@@ -108,8 +117,9 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len,
     // (Counting runs of equal buckets across the lanes first, one add per
     // run, measured slower here: 0.18 against 0.13 ms on the 100^3 cube.)
     // buckets [b_lo, b_lo + nb) only; the others belong to another pass
+    uint32_t bad = 0;
     auto count = [&](int32_t j) {
-        const uint32_t b = ((uint32_t)(checked_index(j, n, st) - 1) >> cs) - (uint32_t)b_lo;
+        const uint32_t b = (zero_based(j, n, bad) >> cs) - (uint32_t)b_lo;
         if (!RANGED || b < (uint32_t)nb) atomicAdd(&s_h[b], 1u);   // one pass: every bucket is in range
     };
     // scalar head up to a 16-byte boundary, int4 body, scalar tail
@@ -127,6 +137,7 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len,
     } else {
         for (int64_t k = c0 + tid; k < c1; k += blockDim.x) count(jj[k]);
     }
+    if (bad) atomicOr(&st->bad_index, 1u);
     __syncthreads();
     uint32_t m = 0;
     for (int b = tid; b < nb; b += blockDim.x) {
@@ -166,9 +177,10 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
     // One position reservation per run of equal buckets across the lanes of
     // a warp: the head lane adds the run's length, every lane of the run
     // takes head's base + its distance to the head (lane order).
+    uint32_t bad = 0;
     auto put = [&](int32_t i, int32_t j, int64_t k, bool have) {
-        const uint32_t i0 = have ? (uint32_t)(checked_index(i, m, st) - 1) : 0u;
-        const uint32_t j0 = have ? (uint32_t)(checked_index(j, n, st) - 1) : 0u;
+        const uint32_t i0 = have ? zero_based(i, m, bad) : 0u;
+        const uint32_t j0 = have ? zero_based(j, n, bad) : 0u;
         const uint32_t bl = (j0 >> cs) - (uint32_t)b_lo;   // bucket inside this pass's range
         if (RANGED) have = have && bl < (uint32_t)nb;
         const uint32_t b = have ? bl : 0xffff0000u | (uint32_t)lane;
@@ -209,6 +221,7 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
     } else {
         scalar(c0, c1);
     }
+    if (bad) atomicOr(&st->bad_index, 1u);
 }
 
 // ----------------------------------------------------------------------------
