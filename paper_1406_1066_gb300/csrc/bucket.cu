@@ -95,6 +95,14 @@ bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fspars
 //      final total passes through some block's old + count).  The order of
 //      the blocks inside a bucket is therefore arbitrary, as is the order
 //      inside a block's range: the emit kernel restores ascending k.
+// in_range for 32-bit values (one unsigned compare); the per-item checks of
+// these kernels use it.
+__device__ __forceinline__ bool in_range32(uint32_t v, uint32_t bound, DevStatus *st) {
+    if (v < bound) return true;
+    if (st) atomicOr(&st->oob, 1u);
+    return false;
+}
+
 // Zero-based index, clamped into [0, dim); an index below 1 or above dim
 // sets `bad` (reported once per thread).  The clamp keeps every address in
 // range, and both kernels map a bad index the same way.
@@ -191,7 +199,7 @@ __global__ void __launch_bounds__(1024, 2) bucket_scatter_kernel(const int32_t *
         if (have && head == lane) base = atomicAdd(&s_cur[b], c);
         const uint32_t pos = __shfl_sync(0xffffffffu, base, head) + (uint32_t)(lane - head);
         const uint64_t w = ((uint64_t)(j0 & lowmask) << (rb + kb)) | ((uint64_t)i0 << kb) | (uint64_t)k;
-        if (have && in_range(pos, len, st)) words[pos] = w;
+        if (have && in_range32(pos, (uint32_t)len, st)) words[pos] = w;
     };
     // 16-byte index loads (four consecutive triplets per thread) when both
     // arrays are 16-byte aligned; scalar head and tail around the aligned body
@@ -457,7 +465,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                 const uint32_t roff = ((uint32_t)(w >> kb) & rbm) - row_lo;
                 const uint32_t rank = s_pref[roff >> 5] + __popc(s_bits[roff >> 5] & ((1u << (roff & 31)) - 1u));
                 const uint32_t kk = (uint32_t)(w >> (kb + rb)) * R + rank;
-                if (in_range(kk, K, a.st)) {
+                if (in_range32(kk, K, a.st)) {
                     atomicOr(&s_kb[kk >> 5], 1u << (kk & 31));
                     pk[i] = (w & kmask) | ((uint64_t)kk << 30) | ((uint64_t)roff << 46);
                 }
@@ -493,7 +501,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             if (w != ~0ull) {
                 const uint32_t kk = (uint32_t)(w >> 30) & 0xffffu;
                 const uint32_t slot = s_kpref[kk >> 5] + __popc(s_kb[kk >> 5] & ((1u << (kk & 31)) - 1u));
-                if (in_range(slot, nx, a.st)) {
+                if (in_range32(slot, (uint32_t)nx, a.st)) {
                     const uint32_t place = atomicAdd(&s_cnt[slot], 1u);
                     s_roff[slot] = (uint16_t)(w >> 46);   // the same value from every triplet of the slot
                     pk[i] = (w & kmask) | ((uint64_t)slot << 30) | ((uint64_t)place << 43);
@@ -531,7 +539,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             if (pk[i] != ~0ull) {
                 const uint32_t slot = (uint32_t)(pk[i] >> 30) & 0x1fffu;
                 const uint32_t q = s_lo[slot] + (uint32_t)(pk[i] >> 43);
-                if (in_range(q, nx, a.st)) {
+                if (in_range32(q, (uint32_t)nx, a.st)) {
                     s_k[q] = (uint32_t)(pk[i] & kmask);
                     s_slot[q] = (uint16_t)slot;
                 }
@@ -559,7 +567,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
             const int q = warp * 32 * IPT + i * 32 + lane;
             if (q >= nx) continue;
             const uint32_t kq = s_k[q], slot = s_slot[q];
-            if (!in_range(slot, U, a.st)) continue;
+            if (!in_range32(slot, U, a.st)) continue;
             const int lo = s_lo[slot], hi = s_lo[slot + 1];
             int dest = q;
             if (hi - lo > 1) {
@@ -640,7 +648,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
         for (int i = 0; i < IPT; ++i) {
             if (valid[i]) {
                 const uint32_t q = s_local[dig[i]] + s_wcnt[warp * 256 + dig[i]] + rnk[i];
-                if (in_range(q, nx, a.st)) s_w[q] = pk[i];
+                if (in_range32(q, (uint32_t)nx, a.st)) s_w[q] = pk[i];
             }
         }
         __syncthreads();
