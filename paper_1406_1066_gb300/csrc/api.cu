@@ -203,24 +203,35 @@ static DevStatus *host_status() {
     return h;
 }
 
-// Wait for the stream's work: poll it for up to kPollMs, then block.  A
-// blocking wait returns some tens of microseconds after the GPU finishes
-// (the thread has to be woken), which the caller of a full assembly pays
-// once per call; polling returns within a microsecond or two.  Longer waits
-// block, so a long queue costs no more than kPollMs of host time.
+// Waits on the host: poll for up to kPollMs, then block.  A blocking wait
+// returns some tens of microseconds after the GPU finishes (the thread has
+// to be woken), which a caller pays at every synchronisation of a call;
+// polling returns within a microsecond or two.  Longer waits block, so a
+// long queue costs no more than kPollMs of host time.
 constexpr double kPollMs = 10.0;
 
-static fsparse_status wait_stream(cudaStream_t s) {
+template <typename Query, typename Block>
+static fsparse_status poll_then_block(Query query, Block block, const char *what) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
-        const cudaError_t q = cudaStreamQuery(s);
+        const cudaError_t q = query();
         if (q == cudaSuccess) return FSPARSE_OK;
-        if (q != cudaErrorNotReady) return cuda_error(q, "cudaStreamQuery");
+        if (q != cudaErrorNotReady) return cuda_error(q, what);
         if (std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() > kPollMs)
             break;
     }
-    FSP_CUDA(cudaStreamSynchronize(s));
-    return FSPARSE_OK;
+    const cudaError_t b = block();
+    return b == cudaSuccess ? FSPARSE_OK : cuda_error(b, what);
+}
+
+fsparse_status wait_stream(cudaStream_t s) {
+    return poll_then_block([&] { return cudaStreamQuery(s); }, [&] { return cudaStreamSynchronize(s); },
+                           "cudaStreamSynchronize");
+}
+
+fsparse_status wait_event(cudaEvent_t e) {
+    return poll_then_block([&] { return cudaEventQuery(e); }, [&] { return cudaEventSynchronize(e); },
+                           "cudaEventSynchronize");
 }
 
 static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) {

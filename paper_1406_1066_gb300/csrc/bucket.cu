@@ -914,7 +914,7 @@ fsparse_status bucket_symbolic(const int32_t *ii, const int32_t *jj, int64_t len
             FSP_LAUNCHED();
         }
         phase_mark("bucket_scatter");
-        FSP_CUDA(cudaEventSynchronize(got_largest));
+        if ((e = wait_event(got_largest)) != FSPARSE_OK) return e;
         largest = *h_largest;
         if (largest <= (uint32_t)kMaxBucketCap) break;
         if (sh.cs == 0 || attempt >= 3) {   // a column (or a few) beyond the cap: onesweep instead

@@ -95,6 +95,9 @@ struct Batch {
 // ---- errors ---------------------------------------------------------------
 fsparse_status set_error(fsparse_status st, const std::string &msg);
 fsparse_status cuda_error(cudaError_t e, const char *what);
+// Host waits that poll briefly before blocking (api.cu).
+fsparse_status wait_stream(cudaStream_t s);
+fsparse_status wait_event(cudaEvent_t e);
 
 // Host-side fault injection for the failure paths, read from the environment
 // at each call: FSPARSE_FAULT=alloc makes every device allocation report
