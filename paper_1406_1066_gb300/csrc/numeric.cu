@@ -174,7 +174,10 @@ fsparse_status launch_adjoint(const int32_t *irank, int64_t len, const double *d
     if (len == 0) return FSPARSE_OK;
     const int vec = ((reinterpret_cast<uintptr_t>(irank) | reinterpret_cast<uintptr_t>(ds)) & 15) == 0;
     const int64_t work = vec ? (len + 3) / 4 : len;
-    const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count(0) * 8);
+    // Four 256-thread blocks per SM (half the resident threads): on the 100^3
+    // cube 0.206 ms against 0.261 at eight, 0.225 at three and 0.219 at six;
+    // with more threads the gathers from dprS ran slower, not faster.
+    const int grid = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count(0) * 4);
     adjoint_kernel<<<std::max(grid, 1), 256, 0, s>>>(irank, len, dprS, ds, vec, nnz);
     FSP_LAUNCHED();
     return FSPARSE_OK;
