@@ -172,8 +172,11 @@ fsparse_status device_alloc(void **p, size_t bytes, cudaStream_t s) {
     return FSPARSE_OK;
 }
 
-Scratch::~Scratch() {
+Scratch::~Scratch() { release(); }
+
+void Scratch::release() {
     for (int i = 0; i < n_; ++i) cudaFreeAsync(ptrs_[i], s_);
+    n_ = 0;
 }
 
 fsparse_status Scratch::alloc(void **p, size_t bytes) {
@@ -234,14 +237,26 @@ fsparse_status wait_event(cudaEvent_t e) {
                            "cudaEventSynchronize");
 }
 
-static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) {
+// The status read in two halves: queue the copy, then wait for it (work
+// such as freeing the status word's own scratch can be queued in between).
+static fsparse_status post_status(DevStatus *d, cudaStream_t s) {
     DevStatus *h = host_status();
     if (!h) return set_error(FSPARSE_ERR_NOMEM, "cudaMallocHost failed");
     FSP_CUDA(cudaMemcpyAsync(h, d, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    return FSPARSE_OK;
+}
+
+static fsparse_status finish_status(DevStatus *out, cudaStream_t s) {
     fsparse_status e = wait_stream(s);
     if (e != FSPARSE_OK) return e;
-    *out = *h;
+    *out = *host_status();
     return FSPARSE_OK;
+}
+
+static fsparse_status read_status(DevStatus *d, DevStatus *out, cudaStream_t s) {
+    fsparse_status e = post_status(d, s);
+    if (e != FSPARSE_OK) return e;
+    return finish_status(out, s);
 }
 
 void note_use(UseLog &log, cudaStream_t s) {
@@ -458,12 +473,17 @@ static fsparse_status symbolic_impl(const int32_t *ii, const int32_t *jj, const 
         if (cudaMemcpyAsync(&d_st->bad_index, &one, 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "cudaMemcpyAsync"));
     }
-    if ((e = read_status(d_st, &h_st, s)) != FSPARSE_OK) return fail(e);
+    // The scratch (status word included) is freed behind the status copy, so
+    // the frees are queued before the host waits instead of after it.
+    if ((e = post_status(d_st, s)) != FSPARSE_OK) return fail(e);
+    scratch.release();
+    if ((e = finish_status(&h_st, s)) != FSPARSE_OK) return fail(e);
     if (h_st.overflow && !h_st.bad_index && !h_st.timeout) {
         // A column bucket outgrew shared memory: same result through onesweep.
         fsparse_config os = cfg;
         os.strategy = FSPARSE_SORT_ONESWEEP;
         plan->cfg = os;
+        if ((e = scratch.get(&d_st, 1)) != FSPARSE_OK) return fail(e);
         if (cudaMemsetAsync(d_st, 0, sizeof(DevStatus), s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "cudaMemsetAsync"));
         e = run_symbolic(ii, jj, sr, prS, len, *plan, os, d_st, scratch, s, &folded);

@@ -164,6 +164,9 @@ class Scratch {
     Scratch(cudaStream_t s, void *arena, size_t bytes) : s_(s), arena_(static_cast<char *>(arena)), arena_bytes_(bytes) {}
     ~Scratch();
     fsparse_status alloc(void **p, size_t bytes);
+    // Queue the frees of everything allocated so far (stream-ordered after
+    // the work already on the stream); the object can allocate again.
+    void release();
     template <class T>
     fsparse_status get(T **p, size_t count) {
         return alloc(reinterpret_cast<void **>(p), count * sizeof(T));
