@@ -340,11 +340,13 @@ fsparse_status fsparse_shard_offset(const int32_t *in, int64_t len, int64_t add,
  *
  * strategy: FSPARSE_SORT_ONESWEEP = global stable LSD radix sort of the
  * packed (column,row) keys, one kernel per digit with decoupled look-back;
- * FSPARSE_SORT_BUCKET = one stable partition by the high column bits,
- * then one shared-memory pass per column bucket fused with run detection,
- * jcS and the chunk slot bases.  Inside a bucket whose (column, dense row
- * rank) key space fits a 65,536-bit map the unique keys are counted in that
- * bitmap (no sort pass); other buckets take 8-bit radix passes.
+ * FSPARSE_SORT_BUCKET = one partition by the high column bits (a count and
+ * a scatter, each run once per range of 32,768 buckets; order inside a
+ * bucket is not kept), then one shared-memory pass per column bucket fused
+ * with run detection, the ascending-k order inside every run, jcS and the
+ * chunk slot bases.  Inside a bucket whose (column, dense row rank) key
+ * space fits a 65,536-bit map the unique keys are counted in that bitmap (no
+ * sort pass); other buckets take 8-bit radix passes.
  * FSPARSE_SORT_BUCKET_RADIX = the same with the radix passes in every bucket.
  * All give bit-identical results.  A bucket that outgrows shared memory
  * makes the library redo the call with ONESWEEP (same results, more time).
