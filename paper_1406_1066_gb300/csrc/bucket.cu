@@ -86,15 +86,6 @@ bool bucket_supported(int64_t len, int32_t n, const KeyLayout &key, const fspars
     return bucket_shape(len, n, key, cfg, nullptr);
 }
 
-// ----------------------------------------------------------------------------
-// 1+2. per-block bucket counts over a contiguous slice of jj (a shared-memory
-//      table, 16-byte loads), then every non-empty (block, bucket) count
-//      reserves its range inside the bucket with one atomic add on the
-//      bucket's total: goff[g][b] is block g's offset inside bucket b, tot[b]
-//      ends as the bucket's size, and *largest as the largest size (every
-//      final total passes through some block's old + count).  The order of
-//      the blocks inside a bucket is therefore arbitrary, as is the order
-//      inside a block's range: the emit kernel restores ascending k.
 // in_range for 32-bit values (one unsigned compare); the per-item checks of
 // these kernels use it.
 __device__ __forceinline__ bool in_range32(uint32_t v, uint32_t bound, DevStatus *st) {
@@ -112,6 +103,15 @@ __device__ __forceinline__ uint32_t zero_based(int32_t v, int32_t dim, uint32_t 
     return min(z, (uint32_t)dim - 1u);
 }
 
+// ----------------------------------------------------------------------------
+// 1+2. per-block bucket counts over a contiguous slice of jj (a shared-memory
+//      table, 16-byte loads), then every non-empty (block, bucket) count
+//      reserves its range inside the bucket with one atomic add on the
+//      bucket's total: goff[g][b] is block g's offset inside bucket b, tot[b]
+//      ends as the bucket's size, and *largest as the largest size (every
+//      final total passes through some block's old + count).  The order of
+//      the blocks inside a bucket is therefore arbitrary, as is the order
+//      inside a block's range: the emit kernel restores ascending k.
 template <bool RANGED>
 __global__ void bucket_count_kernel(const int32_t *__restrict__ jj, int64_t len, int32_t n, int cs,
                                     int b_lo, int nb, uint32_t *__restrict__ goff, uint32_t *__restrict__ tot,
