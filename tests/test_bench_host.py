@@ -59,3 +59,19 @@ def test_reference_arm_small_cube():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_committed_fold_profile_matches_the_kernel_source():
+    """bench.py reports the fold's DRAM traffic from the committed ncu summary
+    only while its recorded source hash names the current numeric.cu and
+    common.cuh; the summary in the repository must be the current one."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    h = bench.kernel_source_hash("numeric.cu", "common.cuh")
+    traffic = bench.profiled_traffic("numeric_kernel_mesh3d_100.md", h)
+    assert traffic is not None, f"profiles/numeric_kernel_mesh3d_100.md does not name source hash {h}"
+    # DRAM bytes of one launch near the algorithmic 12L + 8nnz of the cube
+    algorithmic = 12 * 93_148_704 + 8 * 14_761_198
+    assert 0.9 * algorithmic < traffic < 1.5 * algorithmic
