@@ -48,7 +48,15 @@ constexpr int64_t kBucketsPerPass = 32768;   // shared-memory table of the count
 constexpr int kMaxBucketPasses = 4;           // more buckets: the count and scatter run once per range
 constexpr int64_t kMaxBuckets = kBucketsPerPass * kMaxBucketPasses;
 constexpr int kMaxColBits = 12;     // 2^cs column counters in shared memory
-constexpr int kRunSortMax = 128;    // longest run put back into k order in the bucket kernel
+// Longest run put back into k order in the bucket kernel.  Each triplet of a
+// run of length r reads the run once (r/4 shared loads), so the rank grows
+// with r; a longer run makes the host redo the whole call with the onesweep
+// sort.  On 2e7 triplets in runs of exactly r (20,000 x 20,000): onesweep
+// alone 1.61 ms; ranked here 1.28 / 2.10 / 2.65 / 3.21 ms for r = 160 / 256 /
+// 384 / 512; a bucket pass thrown away plus onesweep 2.5-2.8 ms.  384 sits
+// at the crossover.  (The paper's first data set, pairs 50 times each and a
+// few drawn two or three times, has runs of 150: 2.99 -> 1.05 ms.)
+constexpr int kRunSortMax = 384;
 constexpr int kRowBits = 1 << 16;   // row ranges up to this are compressed to dense ranks
 constexpr int kKeyBits = 1 << 16;   // (column, row rank) key spaces up to this are counted in a bitmap
 

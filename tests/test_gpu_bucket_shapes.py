@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from gpu_util import assert_same, config, gpu_assemble
+from paper_1406_1066_gb300 import fsparse
 
 pytestmark = pytest.mark.gpu
 
@@ -81,3 +82,32 @@ def test_bucket_ranges_in_two_passes(strategy):
     with config(strategy=strategy, bucket_target=1024):
         g = gpu_assemble(ii, jj, s, m, n)
     assert_same(g, oracle.assemble(ii, jj, s, m, n))
+
+
+def exact_runs(P, r, m, n, seed):
+    """P distinct (i, j) pairs, each exactly r times, shuffled."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    keys = np.unique(g.integers(0, m * n, 2 * P, dtype=np.int64))[:P]
+    idx = np.repeat(np.arange(keys.size), r)
+    g.shuffle(idx)
+    ii = (keys[idx] % m + 1).astype(np.int32)
+    jj = (keys[idx] // m + 1).astype(np.int32)
+    return ii, jj, g.standard_normal(idx.size)
+
+
+@pytest.mark.parametrize("strategy", [2, 3])
+@pytest.mark.parametrize("r,bucket_path", [(300, True), (384, True), (385, False)])
+def test_long_runs_ranked_in_the_bucket_or_handed_over(monkeypatch, strategy, r, bucket_path):
+    """Runs of up to 384 triplets are put into ascending k inside the bucket
+    kernel; a longer one hands the whole call to the onesweep sort (its digit
+    passes then show in the phase timings).  Exact either way."""
+    m = n = 3000
+    ii, jj, s = exact_runs(400, r, m, n, 90 + r)
+    with config(strategy=strategy):
+        monkeypatch.setenv("FSPARSE_TIMING", "1")
+        g = gpu_assemble(ii, jj, s, m, n)
+        names = [p for p, _ in fsparse.fsparse_last_timings()]
+        monkeypatch.delenv("FSPARSE_TIMING")
+    assert_same(g, oracle.assemble(ii, jj, s, m, n))
+    assert "bucket_emit" in names
+    assert ("digit_passes" in names) == (not bucket_path), names
