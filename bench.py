@@ -7,8 +7,10 @@ buffers), as in a time-dependent nonlinear PDE solve.  The metric is
 G triplets/s over the whole job (51 assemblies of L triplets per step);
 the JSON line also reports the full and numeric-only phases separately,
 the HBM roofline of the dominant kernel (the numeric fold), the batched vs
-plain comparison on 256 uneven instances, an end-to-end figure through
-host buffers, clocks, and the CPU oracle timed on a bounded sample.
+plain comparison on 256 uneven instances, the other configurations and
+the paper's own three data sets (with the paper's method timed on the host
+cores beside them), an end-to-end figure through host buffers, clocks,
+and the CPU oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -403,46 +405,55 @@ def batched_vs_plain(torch, fsparse, to_dev, peak, steps: int = 100):
 PER_CONFIG = ("mesh2d_64", "uniform_1e6", "pooled_2e4", "mesh3d_60")
 
 
+def full_and_numeric(torch, fsparse, ii_d, jj_d, s_d, s2, t, reps: int):
+    """Full assembly (median of `reps` calls, no plan reuse) and numeric
+    re-assembly (mean of `reps` launches, alternating two value arrays);
+    returns (full ms, nnz, numeric ms)."""
+    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    prS = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+    out_n = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+    for _ in range(3):
+        fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
+    full = []
+    for _ in range(reps):
+        e0, e1 = mk(), mk()
+        e0.record()
+        _, _, _, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)
+        e1.record()
+        torch.cuda.synchronize()
+        full.append(e0.elapsed_time(e1))
+        nnz = plan.nnz
+        plan.close()
+    _, _, _, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)
+    for _ in range(3):
+        fsparse.numeric(plan, s2, out_n)
+    torch.cuda.synchronize()
+    e0, e1 = mk(), mk()
+    e0.record()
+    for r in range(reps):
+        fsparse.numeric(plan, s2 if r & 1 else s_d, out_n)
+    e1.record()
+    torch.cuda.synchronize()
+    num_ms = e0.elapsed_time(e1) / reps
+    plan.close()
+    return statistics.median(full), nnz, num_ms
+
+
 def per_config(torch, fsparse, to_dev, peak, reps: int = 10, tune: bool = True):
     """Configs other than the benchmark's own, one line each: full assembly
     (median of `reps`, no plan reuse) and numeric re-assembly (mean of
     `reps` launches), with their fractions of the measured copy bandwidth."""
     out = {}
-    mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     for name in PER_CONFIG:
         t = inputs.workload(name)
         ii_d, jj_d, s_d = to_dev(t.ii), to_dev(t.jj), to_dev(t.s)
         s2 = to_dev(inputs.mesh_values(t.L, 77))
-        prS = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
-        out_n = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
         if tune:
             fsparse.autotune(ii_d, jj_d, s_d, t.m, t.n, reps=2)
-        for _ in range(3):
-            fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
+        prS = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+        fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
         phases = full_phases(torch, fsparse, ii_d, jj_d, s_d, t, prS, reps=3)
-        full = []
-        for _ in range(reps):
-            e0, e1 = mk(), mk()
-            e0.record()
-            _, _, _, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)
-            e1.record()
-            torch.cuda.synchronize()
-            full.append(e0.elapsed_time(e1))
-            nnz = plan.nnz
-            plan.close()
-        _, _, _, plan = fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)
-        for _ in range(3):
-            fsparse.numeric(plan, s2, out_n)
-        torch.cuda.synchronize()
-        e0, e1 = mk(), mk()
-        e0.record()
-        for r in range(reps):
-            fsparse.numeric(plan, s2 if r & 1 else s_d, out_n)
-        e1.record()
-        torch.cuda.synchronize()
-        num_ms = e0.elapsed_time(e1) / reps
-        plan.close()
-        f_ms = statistics.median(full)
+        f_ms, nnz, num_ms = full_and_numeric(torch, fsparse, ii_d, jj_d, s_d, s2, t, reps)
         B_full = 16 * t.L + 12 * nnz + 4 * (t.n + 1)
         B_num = 12 * t.L + 8 * nnz
         out[name] = {"L": t.L, "nnz": nnz, "m": t.m, "n": t.n,
@@ -453,7 +464,52 @@ def per_config(torch, fsparse, to_dev, peak, reps: int = 10, tune: bool = True):
                      "full_phases_ms": phases, "launch": fsparse.fsparse_get_config(t.L, t.m, t.n),
                      "inputs_vs_l2": "inside L2 (fractions not meaningful)" if 16 * t.L < 64e6
                      else "inputs larger than L2"}
-        del ii_d, jj_d, s_d, s2, prS, out_n
+        del ii_d, jj_d, s_d, s2, prS
+        torch.cuda.empty_cache()
+    return out
+
+
+# The paper's own benchmark sets (§4.2, ransparse(siz, nnz_row, nrep): every
+# row nnz_row times, uniform columns, every pair nrep times, shuffled, values
+# one; 25,000,000 triplets each) and the paper's times for them in seconds,
+# serial and parallel fsparse on its 6-core (C1) and 16-core (C2) hosts (§4.3,
+# table of overall speedups).  Those hosts are other machines: context only.
+PAPER_DATA = {
+    "data1": ((10_000, 50, 50), {"C1": {"serial_s": 1.51, "parallel_s": 0.65},
+                                 "C2": {"serial_s": 1.61, "parallel_s": 0.33}}),
+    "data2": ((50_000, 50, 10), {"C1": {"serial_s": 1.87, "parallel_s": 0.83},
+                                 "C2": {"serial_s": 2.95, "parallel_s": 0.46}}),
+    "data3": ((50_000, 10, 50), {"C1": {"serial_s": 1.67, "parallel_s": 0.76},
+                                 "C2": {"serial_s": 1.78, "parallel_s": 0.43}}),
+}
+
+
+def paper_data(torch, fsparse, to_dev, peak, cpu: bool, reps: int = 10):
+    """Full assembly and numeric re-assembly of the paper's three data sets on
+    the GPU, with their device phases, and (with `cpu`) the paper's own method
+    on the host cores on the same sets, beside the times the paper prints."""
+    out = {}
+    for name, ((siz, nnz_row, nrep), published) in PAPER_DATA.items():
+        t = inputs.ransparse(siz, nnz_row, nrep, seed=1100 + int(name[-1]))
+        ii_d, jj_d, s_d = to_dev(t.ii), to_dev(t.jj), to_dev(t.s)
+        s2 = to_dev(inputs.mesh_values(t.L, 78))
+        prS = torch.empty(t.L, dtype=torch.float64, device=s_d.device)
+        fsparse.assemble(ii_d, jj_d, s_d, t.m, t.n, prS=prS)[3].close()
+        phases = full_phases(torch, fsparse, ii_d, jj_d, s_d, t, prS, reps=3)
+        f_ms, nnz, num_ms = full_and_numeric(torch, fsparse, ii_d, jj_d, s_d, s2, t, reps)
+        B_full = 16 * t.L + 12 * nnz + 4 * (t.n + 1)
+        B_num = 12 * t.L + 8 * nnz
+        row = {"siz": siz, "nnz_row": nnz_row, "nrep": nrep, "L": t.L, "nnz": nnz,
+               "full_ms": f_ms, "full_gtps": t.L / f_ms / 1e6,
+               "full_hbm_frac": B_full / (f_ms / 1e3) / 1e9 / peak,
+               "numeric_ms": num_ms, "numeric_gtps": t.L / num_ms / 1e6,
+               "numeric_hbm_frac": B_num / (num_ms / 1e3) / 1e9 / peak,
+               "full_phases_ms": phases, "launch": fsparse.fsparse_get_config(t.L, t.m, t.n),
+               "paper_published": published}
+        if cpu:
+            row["paper_method_on_host"] = paper_method_job(t, 1)
+        out[name] = row
+        del ii_d, jj_d, s_d, s2, prS
         torch.cuda.empty_cache()
     return out
 
@@ -647,6 +703,7 @@ def gpu_arm(args):
         extra["batched_vs_plain"] = batched_vs_plain(torch, fsparse, to_dev, peak)
     if rank == 0 and world == 1 and not args.no_configs:
         extra["per_config"] = per_config(torch, fsparse, to_dev, peak, tune=not args.no_tune)
+        extra["paper_data"] = paper_data(torch, fsparse, to_dev, peak, cpu=not args.no_cpu)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -708,7 +765,8 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-configs", action="store_true", help="skip the other configs' lines")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configs' lines and the paper's data sets")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch configuration")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="mesh3d_100 (default), or mesh3d_<N> for a smaller cube (profiling)")
