@@ -588,6 +588,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                     // in the next region at worst).
                     const uint32_t len = (uint32_t)(hi - lo);
                     int rank = 0;
+                    // unrolled by 4 so the loads of a long run overlap (symbolic on the
+                    // 100^3 cube 1.59 -> 1.56 ms, 60^3 0.478 -> 0.465; by 2 no gain)
+#pragma unroll 4
                     for (int r = lo & ~3; r < hi; r += 4) {
                         const uint4 f = *reinterpret_cast<const uint4 *>(s_k + r);
                         const uint32_t o = (uint32_t)(r - lo);
@@ -761,6 +764,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) bucket_emit_kernel(Bu
                     const uint32_t kl = (uint32_t)v;
                     const uint32_t len = (uint32_t)(hi - lo);
                     int rank = 0;
+#pragma unroll 4
                     for (int q = lo & ~1; q < hi; q += 2) {
                         const uint4 two = *reinterpret_cast<const uint4 *>(s_w32 + 2 * q);
                         const uint32_t o = (uint32_t)(q - lo);
