@@ -75,3 +75,22 @@ def test_committed_fold_profile_matches_the_kernel_source():
     # DRAM bytes of one launch near the algorithmic 12L + 8nnz of the cube
     algorithmic = 12 * 93_148_704 + 8 * 14_761_198
     assert 0.9 * algorithmic < traffic < 1.5 * algorithmic
+
+
+def test_paper_data_sets_match_the_paper_table():
+    """The benchmark's copy of the paper's data sets (§4.2): 25,000,000
+    triplets each, the same parameters as the parity tests, and the paper's
+    printed serial/parallel seconds (§4.3), parallel faster on every host."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import test_gpu_paper_data as pd
+    assert set(bench.PAPER_DATA) == set(pd.DATA)
+    for name, ((siz, nnz_row, nrep), published) in bench.PAPER_DATA.items():
+        assert (siz, nnz_row, nrep) == pd.DATA[name]
+        assert siz * nnz_row * nrep == 25_000_000
+        assert set(published) == {"C1", "C2"}
+        for host in published.values():
+            assert 0 < host["parallel_s"] < host["serial_s"]
