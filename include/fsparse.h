@@ -348,8 +348,9 @@ fsparse_status fsparse_shard_offset(const int32_t *in, int64_t len, int64_t add,
  * space fits a 65,536-bit map the unique keys are counted in that bitmap (no
  * sort pass); other buckets take 8-bit radix passes.
  * FSPARSE_SORT_BUCKET_RADIX = the same with the radix passes in every bucket.
- * All give bit-identical results.  A bucket that outgrows shared memory
- * makes the library redo the call with ONESWEEP (same results, more time).
+ * All give bit-identical results.  A bucket that outgrows shared memory, or
+ * one (i,j) pair repeated more than 384 times, makes the library redo the
+ * call with ONESWEEP (same results, more time).
  * ---------------------------------------------------------------------- */
 typedef enum fsparse_strategy {
     FSPARSE_SORT_AUTO = 0,
@@ -360,7 +361,7 @@ typedef enum fsparse_strategy {
 
 typedef struct fsparse_config {
     int32_t strategy;        /* fsparse_strategy                                 */
-    int32_t radix_bits;      /* ONESWEEP digit width, 6..8                       */
+    int32_t radix_bits;      /* ONESWEEP digit width, 6..8 (9, 10: 256 threads)  */
     int32_t sweep_items;     /* ONESWEEP items per thread: 8, 12 or 16            */
     int32_t sweep_threads;   /* ONESWEEP threads per block: 256 or 512            */
     int32_t bucket_target;   /* BUCKET mean items per bucket, 1024..16384         */
